@@ -1,0 +1,245 @@
+/*
+ * cdc.h -- C ABI of the GB300 seed-scanning track finder for a cylindrical
+ * drift chamber (arXiv:1908.01949, "GPU Tracking in the COMET Phase-I
+ * Cylindrical Drift Chamber").
+ *
+ * Conventions (all entry points):
+ *   - Units: mm, MeV/c, T, rad.  A seed is the float32 vector
+ *     (theta0, z0, px0, py0, pz0) at the cylinder r = R0 (sec. 2.1: the seed
+ *     is defined in front of the first layer, so only five of its six
+ *     parameters are scanned).
+ *   - "host" pointers are read during the call and not kept; "device" pointers
+ *     must be cudaMalloc'ed memory of the context's device (e.g. torch CUDA
+ *     tensors).  The caller owns every buffer it passes.
+ *   - Compute calls are asynchronous on the given stream (cudaStream_t passed
+ *     as void*, NULL = legacy default stream); they allocate nothing and do not
+ *     synchronise.  They return CDC_OK once the work is enqueued.
+ *   - Errors: every call returns a cdc_status; cdc_last_error(ctx) gives a
+ *     one-line reason.  Argument errors are detected before anything is
+ *     enqueued.  Per-event conditions (step cap reached, full found-hit list,
+ *     empty event) are warning bits in the per-event flags output, never
+ *     aborts.
+ *   - Hits are given per event in CSR form: hit_off[e] .. hit_off[e+1] index
+ *     wire_id[] / drift[]; one hit per fired wire (sec. 2.2: the sum of Eq. 1
+ *     runs over wires).
+ */
+#ifndef CDC_H
+#define CDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDC_MAX_LAYERS 64
+#define CDC_MAX_WIRES 8192
+#define CDC_MAX_K 64
+#define CDC_MAX_ZOOM 8
+#define CDC_MAX_ROUNDS 16
+#define CDC_MAX_FOUND 128 /* per-seed list of wires scored below lambda */
+
+typedef struct cdc_ctx cdc_ctx;
+
+typedef enum {
+    CDC_OK = 0,
+    CDC_ERR_ARG = -1,        /* null pointer, negative size, inconsistent parameter */
+    CDC_ERR_RANGE = -2,      /* a size or value beyond a documented limit */
+    CDC_ERR_CUDA = -3,       /* a CUDA runtime call failed (message in cdc_last_error) */
+    CDC_ERR_NOT_LOADED = -4, /* geometry or field not loaded, or workspace too small */
+    CDC_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+    CDC_ERR_NOMEM = -6       /* device allocation failed (only in create/load/reserve) */
+} cdc_status;
+
+/* Per-event warning flags (bitmask). */
+#define CDC_FLAG_STEP_CAP 1u        /* some seed stopped at max_steps */
+#define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed found more than CDC_MAX_FOUND wires below lambda */
+#define CDC_FLAG_EMPTY 4u           /* no hits, no seeds, or no Hough candidate */
+#define CDC_FLAG_NOT_SPD 8u         /* refine: normal matrix regularised */
+#define CDC_FLAG_DOCA_ZERO 16u      /* refine: a hit at zero distance was left out */
+#define CDC_FLAG_LOST_HIT 32u       /* refine: an assigned hit had no minimum in its partition */
+#define CDC_FLAG_BAD_HIT 64u        /* wire id out of range, duplicate wire, or drift outside [0, max_drift] */
+
+/* One seed grid: the seeds are centre[a] + (i_a - (n[a]-1)/2) * step[a] for
+ * i_a in [0, n[a]), enumerated row-major over (theta0, z0, px0, py0, pz0);
+ * each value is the float32 nearest that exact number. */
+typedef struct {
+    float centre[5];
+    float step[5];
+    int32_t n[5];
+} cdc_grid;
+
+/* Parameters of the seed scan (sec. 2.2). */
+typedef struct {
+    float h;                /* RKN step length [mm], > 0 */
+    int32_t max_steps;      /* propagation cap per seed, 1 .. 1<<20 */
+    float lambda;           /* cutoff of Eq. 1 [mm^2], > 0 */
+    int32_t max_partitions; /* turn partitions followed per seed, 1 .. 16 */
+    int32_t direction;      /* +1 propagate along p, -1 against p (exit seeds) */
+    float charge;           /* particle charge [e], -1 for the electron */
+    int32_t k;              /* best seeds kept per event, 1 .. CDC_MAX_K */
+    int32_t n_rounds;       /* scan rounds: 1 coarse + (n_rounds-1) zoom rounds, 1 .. CDC_MAX_ROUNDS */
+    int32_t n_zoom;         /* candidates re-scanned per zoom round, 1 .. min(k, CDC_MAX_ZOOM) */
+    float max_drift;        /* upper bound of every drift value [mm]; sizes the wire search window */
+} cdc_scan_params;
+
+/* Parameters of the circle Hough transform (sec. 2.1, Fig. 4). */
+typedef struct {
+    int32_t n_bins;         /* accumulator n_bins x n_bins over the circle centre (x0, y0), <= 4096 */
+    int32_t bin_um;         /* bin width [um], even, > 0 */
+    int32_t origin_um;      /* coordinate of the lower edge of bin 0 [um] (both axes) */
+    int32_t n_r;            /* radii R_j = r_min_um + j r_step_um, j < n_r <= 256 */
+    int32_t r_min_um;
+    int32_t r_step_um;
+    int32_t n_phi;          /* vote angles 2 pi k / n_phi, <= 8192 */
+    int32_t target_um;      /* circle must pass within this distance of the axis */
+    int32_t min_peak;       /* absolute peak threshold */
+    int32_t max_cand;       /* candidates kept per event, 1 .. 64 */
+    int32_t r_hist_half_um; /* half width of the radius histogram bins [um] */
+    float b_nominal;        /* field used to turn the radius into pT [T] */
+    float charge;           /* particle charge [e] (sets the sense of rotation) */
+    cdc_grid grid_template; /* steps/counts of all axes and the z0, pz0 centres of the output grid */
+} cdc_hough_params;
+
+typedef struct {
+    int32_t ix, iy, count, r_bin; /* peak bin, votes, radius bin (-1 if none) */
+    float theta0, px0, py0;       /* seed centre where the circle meets r = R0 moving outward (NaN if never) */
+} cdc_candidate;
+
+/* Parameters of the Gauss-Newton refinement (not in the paper). */
+typedef struct {
+    int32_t n_iter;         /* Gauss-Newton iterations, 0 .. 32 */
+    float sigma;            /* drift resolution in the chi^2 [mm], > 0 */
+    float scale[5];         /* parameter scales of the normal equations */
+    int32_t checkpoint;     /* adjoint checkpoint interval in steps, 8 .. 512 */
+} cdc_refine_params;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: CDC_ERR_ARG (out NULL), CDC_ERR_CUDA (device unusable). */
+int cdc_create(cdc_ctx** out, int device);
+
+/* Release the context and all device memory it owns.  NULL is ignored. */
+void cdc_destroy(cdc_ctx* ctx);
+
+/* Reason for the last failed call on ctx (static string, never NULL). */
+const char* cdc_last_error(const cdc_ctx* ctx);
+
+/* ---- loading (copy host data into the context; synchronous) ------------ */
+
+/* Sense-layer geometry (sec. 1: eighteen stereo layers).  Host arrays of
+ * n_layers entries, layers ordered by increasing R: waist radius R [mm] at
+ * z = 0, stereo angle alpha [rad], wires N, azimuth phi_off [rad] of wire 0.
+ * Wire i of layer l sits at azimuth phi_off + 2 pi i / N at z = 0, direction
+ * (-sin a sin phi, sin a cos phi, cos a); global wire ids run layer by layer.
+ * z_half: active half length; R0: seed cylinder (sec. 2.1); R_out: outer
+ * stop radius.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE (n_layers > 64, total
+ * wires > 8192, R not increasing, R0 >= R[0]), CDC_ERR_NOMEM. */
+int cdc_load_geometry(cdc_ctx* ctx, int n_layers, const double* R, const double* alpha, const int32_t* N,
+                      const double* phi_off, double z_half, double R0, double R_out);
+
+/* Magnetic field (sec. 1: 1 T solenoid; sec. 2.2: the field is copied to the
+ * device).  kind 0: uniform (0, 0, b0).  kind 1: axisymmetric map, host
+ * arrays bz, br of nr x nz float32 samples (index ir*nz + iz) at r = r_min +
+ * ir dr, z = z_min + iz dz; the field is their bilinear interpolation with
+ * coordinates clamped to the grid, Bx = Br x/r, By = Br y/r.
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE (nr, nz < 2), CDC_ERR_NOMEM. */
+int cdc_load_field(cdc_ctx* ctx, int kind, float b0, const float* bz, const float* br, int nr, int nz,
+                   float r_min, float z_min, float dr, float dz);
+
+/* Size the context's workspace for calls with up to max_events events,
+ * max_seeds seeds in total per scan round, and max_hits hits.  Compute calls
+ * never allocate; a call that exceeds the reservation fails with
+ * CDC_ERR_NOT_LOADED.  Errors: CDC_ERR_ARG, CDC_ERR_NOMEM. */
+int cdc_reserve(cdc_ctx* ctx, int max_events, int64_t max_seeds, int64_t max_hits);
+
+/* ---- compute ------------------------------------------------------------ */
+
+/* Circle Hough transform and seed-grid centre (sec. 2.1, Fig. 4).  For each
+ * event, every hit (its wire at z = 0, rounded to integer um) votes, for each
+ * radius R_j and angle phi_k, for the centre X + round(R_j (cos, sin) phi_k)
+ * if that circle passes within target_um of the axis; integer arithmetic, so
+ * the accumulator is bit-exact in any vote order.  Peaks: count >=
+ * max(min_peak, ceil(max/2)), strict 3x3 maxima (equal neighbours resolved to
+ * the lower linear index), ordered by (count desc, index asc).  Radius of a
+ * peak: the R_j whose [R_j - half, R_j + half) holds most hits.
+ * Device inputs: hit_off [n_events+1], wire_id [hits].  Device outputs:
+ * acc [n_events][n_bins][n_bins] int32 (row = y bin; overwritten),
+ * cand [n_events][max_cand], n_cand [n_events], grid_out [n_events] (nullable:
+ * the top candidate's theta0, px0, py0 with the template's other fields; a
+ * grid of zero seeds if there is no candidate), flags [n_events].
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
+int cdc_hough_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id,
+                    const cdc_hough_params* params, int32_t* acc, cdc_candidate* cand, int32_t* n_cand,
+                    cdc_grid* grid_out, uint32_t* flags, void* stream);
+
+/* Seed scan (sec. 2.2, Eq. 1).  For every seed of grids[e] the track is
+ * propagated by RKN steps of length h and scored
+ *     E = sum over the event's hits of min( min_k (|DCA_k| - drift)^2, lambda ),
+ * DCA_k the distance of closest approach of the continuous track to the wire
+ * line within turn partition k (partition k+1 starts at the k-th inward
+ * crossing of R0; propagation ends after max_partitions partitions, at
+ * |z| > z_half, at r > R_out or after max_steps).  The k best seeds of the
+ * coarse grid are kept (order: E, then index), the n_zoom best are re-scanned
+ * on 3^5 grids with half the previous step, n_rounds-1 times (sec. 2.2: finer
+ * seed sets around the candidates, repeated), and each event's hits are
+ * classified for its overall best seed (d^2 < lambda -> partition, else -1).
+ * Device inputs: hit_off [n_events+1], wire_id, drift [hits], grids
+ * [n_events].  Device outputs: E [sum of grid sizes] (nullable; coarse-round
+ * scores, events concatenated), topk0 [n_events][k] (nullable; coarse-round
+ * keys (float bits of E << 32) | seed index), best_E [n_events][k],
+ * best_seed [n_events][k][5] (best over all rounds), hit_part [hits]
+ * (nullable), hit_res2 [hits] (nullable; best squared residual of the best
+ * seed), zoom_grids [n_rounds][n_events][n_zoom] (nullable; the grids of each
+ * round, round 0 in slot 0), flags [n_events], steps (nullable, 1 counter:
+ * RKN steps executed, accumulated).
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
+int cdc_scan_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id,
+                   const float* drift, const cdc_grid* grids, const cdc_scan_params* params, float* E,
+                   uint64_t* topk0, float* best_E, float* best_seed, int8_t* hit_part, float* hit_res2,
+                   cdc_grid* zoom_grids, uint32_t* flags, unsigned long long* steps, void* stream);
+
+/* Gauss-Newton refinement of seeds (not in the paper; it refines the scan's
+ * surviving seeds in place of the Kalman fit of sec. 2.2).  Each seed first
+ * classifies its event's hits as the scan does (d^2 < lambda -> partition);
+ * then n_iter iterations minimise chi^2 = sum over classified hits of
+ * ((DCA_k - drift)/sigma)^2 with J from forward tangents of the RKN step and
+ * an FP64 Cholesky solve of the 5x5 normal equations in units of scale.
+ * Device inputs: seed_event [n_seeds] (event of each seed), seeds
+ * [n_seeds][5], hit_off, wire_id, drift.  Device outputs: seeds_out
+ * [n_seeds][5], chi2 [n_seeds] (FP64, at the refined seed), grad [n_seeds][5]
+ * (nullable; d chi^2 / d seed at the refined seed from the adjoint RKN with
+ * checkpoints every `checkpoint` steps), n_used [n_seeds] (nullable), flags
+ * [n_seeds].  scan supplies h, max_steps, lambda, max_partitions, direction,
+ * charge, max_drift.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED,
+ * CDC_ERR_CUDA. */
+int cdc_refine_seeds(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds,
+                     const int32_t* hit_off, const int32_t* wire_id, const float* drift,
+                     const cdc_scan_params* scan, const cdc_refine_params* params, float* seeds_out,
+                     double* chi2, float* grad, int32_t* n_used, uint32_t* flags, void* stream);
+
+/* chi^2 of fixed seeds and its gradient by the adjoint RKN kernel (the
+ * backward half of cdc_refine_seeds, exposed for autograd).  Hit
+ * classification as in cdc_refine_seeds, at the given seed.  Device outputs:
+ * chi2 [n_seeds] (FP64), grad [n_seeds][5] (nullable).  Errors as above. */
+int cdc_chi2_grad(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds,
+                  const int32_t* hit_off, const int32_t* wire_id, const float* drift,
+                  const cdc_scan_params* scan, const cdc_refine_params* params, double* chi2, float* grad,
+                  int32_t* n_used, uint32_t* flags, void* stream);
+
+/* Recorded propagation (the RKN of sec. 2.2, for checking propagated
+ * positions and for the precision sweep).  Each seed is propagated with the
+ * scan's stop rules; every `every` steps (starting at step `every`) the
+ * position is written, up to n_rec records.  precision 0: FP32 with
+ * compensated state (the scan's stepper); 1: FP64.  Device outputs: pos
+ * [n_seeds][n_rec][3] float64 (NaN after the track ended), n_steps [n_seeds],
+ * path [n_seeds] (FP64 path length).  Errors as above. */
+int cdc_propagate(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_params* scan, int every,
+                  int n_rec, int precision, double* pos, int32_t* n_steps, double* path, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDC_H */

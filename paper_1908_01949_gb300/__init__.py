@@ -1,0 +1,121 @@
+"""GB300 seed-scanning track finder for a cylindrical drift chamber
+(arXiv:1908.01949, "GPU Tracking in the COMET Phase-I Cylindrical Drift
+Chamber").
+
+The compute path is the CUDA library libcdc.so behind the C ABI of
+include/cdc.h; `Context` exposes its entry points under the same names
+(argument marshalling only) and `Tracker` adds output allocation around them.
+PyTorch provides device memory, streams and autograd.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._lib import (CAND_DTYPE, CDC_MAX_K, CDC_MAX_ZOOM, EXPORTS, FLAG_BAD_HIT, FLAG_DOCA_ZERO, FLAG_EMPTY,
+                   FLAG_FOUND_OVERFLOW, FLAG_LOST_HIT, FLAG_NOT_SPD, FLAG_STEP_CAP, GRID_BYTES, GRID_DTYPE, CdcError,
+                   Context, grids_to_tensor, hough_params, lib, refine_params, scan_params, tensor_to_grids)
+
+__all__ = ["Context", "Tracker", "CdcError", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
+           "tensor_to_grids", "GRID_DTYPE", "CAND_DTYPE", "EXPORTS", "lib"]
+
+
+class Tracker:
+    """A loaded context plus output allocation for the five calls."""
+
+    def __init__(self, geometry, field, device: int = 0, max_events: int = 1, max_seeds: int = 1 << 20,
+                 max_hits: int = 1 << 16):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.ctx = Context(device)
+        g = geometry
+        self.ctx.cdc_load_geometry(g.R, g.alpha, g.N, g.phi_off, g.z_half, g.R0, g.R_out)
+        if field.kind == 0:
+            self.ctx.cdc_load_field(0, field.B0)
+        else:
+            self.ctx.cdc_load_field(1, field.B0, field.bz, field.br, field.bz.shape[0], field.bz.shape[1],
+                                    field.r_min, field.z_min, field.dr, field.dz)
+        self.reserve(max_events, max_seeds, max_hits)
+
+    def reserve(self, max_events, max_seeds, max_hits):
+        self.ctx.cdc_reserve(max_events, max_seeds, max_hits)
+        self.max_events = max_events
+
+    def events_to_device(self, hit_off, wire_id, drift):
+        t = self.torch
+        return (t.as_tensor(np.asarray(hit_off, np.int32), device=self.dev),
+                t.as_tensor(np.asarray(wire_id, np.int32), device=self.dev),
+                t.as_tensor(np.asarray(drift, np.float32), device=self.dev))
+
+    def hough(self, hit_off, wire_id, params, stream=None):
+        t = self.torch
+        ne = int(hit_off.numel()) - 1
+        nb = params.n_bins
+        out = dict(acc=t.empty((ne, nb, nb), dtype=t.int32, device=self.dev),
+                   cand=t.empty((ne, params.max_cand, CAND_DTYPE.itemsize), dtype=t.uint8, device=self.dev),
+                   n_cand=t.empty(ne, dtype=t.int32, device=self.dev),
+                   grid=t.empty((ne, GRID_BYTES), dtype=t.uint8, device=self.dev),
+                   flags=t.empty(ne, dtype=t.int32, device=self.dev))
+        self.ctx.cdc_hough_seeds(ne, hit_off, wire_id, params, out["acc"], out["cand"], out["n_cand"], out["grid"],
+                                 out["flags"], stream)
+        return out
+
+    def scan(self, hit_off, wire_id, drift, grids, params, want_E=False, want_topk0=True, want_hits=True,
+             want_zoom_grids=False, n_seeds=None, stream=None):
+        t = self.torch
+        ne = int(hit_off.numel()) - 1
+        K = params.k
+        out = dict(best_E=t.empty((ne, K), dtype=t.float32, device=self.dev),
+                   best_seed=t.empty((ne, K, 5), dtype=t.float32, device=self.dev),
+                   flags=t.empty(ne, dtype=t.int32, device=self.dev),
+                   steps=t.zeros(1, dtype=t.int64, device=self.dev))
+        out["E"] = t.empty(int(n_seeds), dtype=t.float32, device=self.dev) if want_E else None
+        out["topk0"] = t.empty((ne, K), dtype=t.int64, device=self.dev) if want_topk0 else None
+        nh = int(wire_id.numel())
+        out["hit_part"] = t.empty(max(nh, 1), dtype=t.int8, device=self.dev) if want_hits else None
+        out["hit_res2"] = t.empty(max(nh, 1), dtype=t.float32, device=self.dev) if want_hits else None
+        nz = params.n_zoom if params.n_rounds > 1 else 1
+        out["zoom_grids"] = (t.empty((params.n_rounds, ne, nz, GRID_BYTES), dtype=t.uint8, device=self.dev)
+                             if want_zoom_grids else None)
+        self.ctx.cdc_scan_seeds(ne, hit_off, wire_id, drift, grids, params, out["E"], out["topk0"], out["best_E"],
+                                out["best_seed"], out["hit_part"], out["hit_res2"], out["zoom_grids"], out["flags"],
+                                out["steps"], stream)
+        return out
+
+    def propagate(self, seeds, params, every, n_rec, precision=0, stream=None):
+        t = self.torch
+        n = int(seeds.shape[0])
+        out = dict(pos=t.empty((n, n_rec, 3), dtype=t.float64, device=self.dev),
+                   n_steps=t.empty(n, dtype=t.int32, device=self.dev),
+                   path=t.empty(n, dtype=t.float64, device=self.dev))
+        self.ctx.cdc_propagate(n, seeds, params, every, n_rec, precision, out["pos"], out["n_steps"], out["path"],
+                               stream)
+        return out
+
+    def refine(self, seed_event, seeds, hit_off, wire_id, drift, scan, params, want_grad=True, stream=None):
+        t = self.torch
+        n = int(seeds.shape[0])
+        out = dict(seeds=t.empty((n, 5), dtype=t.float32, device=self.dev),
+                   chi2=t.empty(n, dtype=t.float64, device=self.dev),
+                   grad=t.empty((n, 5), dtype=t.float32, device=self.dev) if want_grad else None,
+                   n_used=t.empty(n, dtype=t.int32, device=self.dev),
+                   flags=t.empty(n, dtype=t.int32, device=self.dev))
+        self.ctx.cdc_refine_seeds(n, seed_event, seeds, hit_off, wire_id, drift, scan, params, out["seeds"],
+                                  out["chi2"], out["grad"], out["n_used"], out["flags"], stream)
+        return out
+
+    def chi2_grad(self, seed_event, seeds, hit_off, wire_id, drift, scan, params, want_grad=True, stream=None):
+        t = self.torch
+        n = int(seeds.shape[0])
+        out = dict(chi2=t.empty(n, dtype=t.float64, device=self.dev),
+                   grad=t.empty((n, 5), dtype=t.float32, device=self.dev) if want_grad else None,
+                   n_used=t.empty(n, dtype=t.int32, device=self.dev),
+                   flags=t.empty(n, dtype=t.int32, device=self.dev))
+        self.ctx.cdc_chi2_grad(n, seed_event, seeds, hit_off, wire_id, drift, scan, params, out["chi2"], out["grad"],
+                               out["n_used"], out["flags"], stream)
+        return out
+
+
+def decode_candidates(t):
+    return np.ascontiguousarray(t.detach().cpu().numpy()).reshape(-1).view(CAND_DTYPE)

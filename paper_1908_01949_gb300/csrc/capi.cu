@@ -1,0 +1,447 @@
+// C ABI of the seed-scanning track finder: context, loading, validation and
+// the compute entry points declared in include/cdc.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/cdc.h"
+#include "cdc_dev.cuh"
+#include "cdc_host.h"
+
+using namespace cdc;
+
+struct cdc_ctx {
+    int device = 0;
+    int num_sms = 1;
+    std::string err;
+    // geometry
+    bool geom = false;
+    DevGeom G{};
+    DevLayer* d_layers = nullptr;
+    float4* d_wires = nullptr;
+    uchar2* d_tab = nullptr;
+    int2* d_wire_um = nullptr;
+    double tan_max = 0.0;
+    // field
+    bool field = false;
+    DevField F{};
+    float4* d_cells = nullptr;
+    // workspace
+    Workspace W{};
+    // Hough vote offsets for the last parameter set
+    int2* d_offsets = nullptr;
+    size_t offsets_cap = 0;
+    int off_key[4] = {-1, -1, -1, -1};
+};
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+int fail(cdc_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(cdc_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, CDC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <class T>
+cudaError_t dalloc(T*& p, size_t n) {
+    dfree(p);
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)&p, n * sizeof(T));
+}
+
+void free_workspace(Workspace& W) {
+    dfree(W.drift_tab);
+    dfree(W.E);
+    dfree(W.seed_off);
+    dfree(W.seg_off);
+    dfree(W.counters);
+    dfree(W.seg_keys);
+    dfree(W.round_keys);
+    dfree(W.best_keys);
+    dfree(W.zgrids);
+    W = Workspace{};
+}
+
+// Window and band half-width [mm] that cover every wire whose distance of
+// closest approach can score below lambda (see tracer.cuh).
+float search_width(const cdc_ctx* c, const cdc_scan_params* p) {
+    double dmax = (double)p->max_drift + sqrt((double)p->lambda);
+    return (float)((1.0 + c->tan_max) * dmax + 1.1 * (double)p->h + 1.0);
+}
+
+int check_scan_params(cdc_ctx* c, const cdc_scan_params* p, bool need_k) {
+    if (!p) return fail(c, CDC_ERR_ARG, "scan params is NULL");
+    if (!(p->h > 0.f) || !(p->lambda > 0.f) || !(p->max_drift >= 0.f) || !(p->charge == p->charge) || p->charge == 0.f)
+        return fail(c, CDC_ERR_ARG, "scan params: h, lambda, charge must be non-zero, max_drift >= 0");
+    if (p->max_steps < 1 || p->max_steps > (1 << 20)) return fail(c, CDC_ERR_RANGE, "max_steps outside 1..2^20");
+    if (p->max_partitions < 1 || p->max_partitions > 16)
+        return fail(c, CDC_ERR_RANGE, "max_partitions outside 1..16");
+    if (p->direction != 1 && p->direction != -1) return fail(c, CDC_ERR_ARG, "direction must be +1 or -1");
+    if (need_k) {
+        if (p->k < 1 || p->k > CDC_MAX_K) return fail(c, CDC_ERR_RANGE, "k outside 1..64");
+        if (p->n_rounds < 1 || p->n_rounds > CDC_MAX_ROUNDS) return fail(c, CDC_ERR_RANGE, "n_rounds outside 1..16");
+        if (p->n_rounds > 1 && (p->n_zoom < 1 || p->n_zoom > CDC_MAX_ZOOM || p->n_zoom > p->k))
+            return fail(c, CDC_ERR_RANGE, "n_zoom outside 1..min(k, 8)");
+    }
+    if (search_width(c, p) > TAB_BAND)
+        return fail(c, CDC_ERR_RANGE, "max_drift + sqrt(lambda) too large for the wire search window");
+    return CDC_OK;
+}
+
+ScanConst make_const(const cdc_ctx* c, const cdc_scan_params* p) {
+    ScanConst P{};
+    P.h = p->h;
+    P.lam = p->lambda;
+    P.charge_dir = p->charge * (float)p->direction;
+    P.band = search_width(c, p);
+    P.d_win = P.band;
+    P.max_drift = p->max_drift;
+    P.max_steps = p->max_steps;
+    P.max_part = p->max_partitions;
+    P.direction = p->direction;
+    P.k = p->k;
+    return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdc_create(cdc_ctx** out, int device) {
+    if (!out) return CDC_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return CDC_ERR_CUDA;
+    cdc_ctx* c = new cdc_ctx();
+    c->device = device;
+    DeviceGuard g(device);
+    if (!g.ok || cudaFree(0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return CDC_ERR_CUDA;
+    }
+    *out = c;
+    return CDC_OK;
+}
+
+void cdc_destroy(cdc_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    dfree(c->d_layers);
+    dfree(c->d_wires);
+    dfree(c->d_tab);
+    dfree(c->d_wire_um);
+    dfree(c->d_cells);
+    dfree(c->d_offsets);
+    free_workspace(c->W);
+    delete c;
+}
+
+const char* cdc_last_error(const cdc_ctx* c) {
+    if (!c) return "NULL context";
+    return c->err.c_str();
+}
+
+int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* alpha, const int32_t* N,
+                      const double* phi_off, double z_half, double R0, double R_out) {
+    if (!c) return CDC_ERR_ARG;
+    if (!R || !alpha || !N || !phi_off) return fail(c, CDC_ERR_ARG, "geometry array is NULL");
+    if (n_layers < 1 || n_layers > CDC_MAX_LAYERS) return fail(c, CDC_ERR_RANGE, "n_layers outside 1..64");
+    if (!(z_half > 0) || !(R0 > 0) || !(R_out > R0)) return fail(c, CDC_ERR_ARG, "need z_half > 0, 0 < R0 < R_out");
+    if (R_out + TAB_BAND + 10.0 >= TAB_N) return fail(c, CDC_ERR_RANGE, "R_out beyond the radial table (990 mm)");
+    int nw = 0;
+    double tmax = 0.0;
+    for (int l = 0; l < n_layers; ++l) {
+        if (N[l] < 3 || N[l] > 65535) return fail(c, CDC_ERR_RANGE, "wires per layer outside 3..65535");
+        if (!(R[l] > TAB_BAND) || (l > 0 && !(R[l] > R[l - 1])))
+            return fail(c, CDC_ERR_RANGE, "layer radii must increase and exceed 24 mm");
+        if (!(fabs(alpha[l]) < 0.19)) return fail(c, CDC_ERR_RANGE, "|stereo angle| must be below 0.19 rad");
+        nw += N[l];
+        tmax = std::max(tmax, fabs(tan(alpha[l])));
+    }
+    if (nw > CDC_MAX_WIRES) return fail(c, CDC_ERR_RANGE, "more than 8192 wires");
+    std::vector<DevLayer> lay(n_layers);
+    std::vector<float4> wires(nw);
+    std::vector<int2> wum(nw);
+    int base = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        DevLayer& L = lay[l];
+        double ta = tan(alpha[l]);
+        L.R2 = (float)(R[l] * R[l]);
+        L.tan2a = (float)(ta * ta);
+        L.tana_over_R = (float)(ta / R[l]);
+        L.phi_off = (float)phi_off[l];
+        L.n_over_2pi = (float)(N[l] / (2.0 * PI));
+        L.cells_per_mm = (float)(N[l] / (2.0 * PI * (R[l] - TAB_BAND)) * 1.01);
+        L.cosa = (float)cos(alpha[l]);
+        L.N = N[l];
+        L.base = base;
+        double sa = sin(alpha[l]);
+        for (int i = 0; i < N[l]; ++i) {
+            double phi = phi_off[l] + 2.0 * PI * (double)i / (double)N[l];
+            double mx = R[l] * cos(phi), my = R[l] * sin(phi);
+            wires[base + i] = make_float4((float)mx, (float)my, (float)(-sa * sin(phi)), (float)(sa * cos(phi)));
+            wum[base + i] = make_int2((int)llround(1000.0 * mx), (int)llround(1000.0 * my));
+        }
+        base += N[l];
+    }
+    // candidate layers per millimetre of rho: bands [R_l - B, r_l(z_half + 10) + B]
+    std::vector<uchar2> tab(TAB_N);
+    for (int b = 0; b < TAB_N; ++b) {
+        int lo = n_layers, hi = -1;
+        for (int l = 0; l < n_layers; ++l) {
+            double ta = tan(alpha[l]);
+            double rmax = sqrt(R[l] * R[l] + (z_half + 10.0) * (z_half + 10.0) * ta * ta);
+            if (rmax + TAB_BAND >= b && R[l] - TAB_BAND <= b + 1) {
+                lo = std::min(lo, l);
+                hi = std::max(hi, l);
+            }
+        }
+        tab[b] = hi < 0 ? make_uchar2(1, 0) : make_uchar2((unsigned char)lo, (unsigned char)hi);
+    }
+    DeviceGuard g(c->device);
+    cudaError_t e;
+    if ((e = dalloc(c->d_layers, lay.size())) != cudaSuccess || (e = dalloc(c->d_wires, wires.size())) != cudaSuccess ||
+        (e = dalloc(c->d_tab, tab.size())) != cudaSuccess || (e = dalloc(c->d_wire_um, wum.size())) != cudaSuccess)
+        return fail(c, CDC_ERR_NOMEM, std::string("geometry allocation: ") + cudaGetErrorString(e));
+    if ((e = cudaMemcpy(c->d_layers, lay.data(), lay.size() * sizeof(DevLayer), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_wires, wires.data(), wires.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_tab, tab.data(), tab.size() * sizeof(uchar2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_wire_um, wum.data(), wum.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "geometry upload");
+    c->G.layers = c->d_layers;
+    c->G.wires = c->d_wires;
+    c->G.tab = c->d_tab;
+    c->G.wire_um = c->d_wire_um;
+    c->G.n_layers = n_layers;
+    c->G.n_wires = nw;
+    c->G.z_half = (float)z_half;
+    c->G.R0 = (float)R0;
+    c->G.R_out = (float)R_out;
+    c->G.R0d = R0;
+    c->tan_max = tmax;
+    c->geom = true;
+    return CDC_OK;
+}
+
+int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float* br, int nr, int nz, float r_min,
+                   float z_min, float dr, float dz) {
+    if (!c) return CDC_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (kind == 0) {
+        if (!(b0 == b0)) return fail(c, CDC_ERR_ARG, "b0 is NaN");
+        c->F = DevField{};
+        c->F.kind = 0;
+        c->F.B0 = b0;
+        c->field = true;
+        return CDC_OK;
+    }
+    if (kind != 1) return fail(c, CDC_ERR_ARG, "field kind must be 0 or 1");
+    if (!bz || !br) return fail(c, CDC_ERR_ARG, "field map array is NULL");
+    if (nr < 2 || nz < 2 || (long long)nr * nz > (1ll << 28)) return fail(c, CDC_ERR_RANGE, "map size");
+    if (!(dr > 0.f) || !(dz > 0.f) || !(r_min >= 0.f)) return fail(c, CDC_ERR_ARG, "need dr, dz > 0 and r_min >= 0");
+    const size_t ncell = (size_t)(nr - 1) * (nz - 1);
+    std::vector<float4> cells(2 * ncell);
+    for (int i = 0; i + 1 < nr; ++i)
+        for (int j = 0; j + 1 < nz; ++j) {
+            const float* m[2] = {bz, br};
+            for (int q = 0; q < 2; ++q) {
+                double v00 = m[q][(size_t)i * nz + j], v10 = m[q][(size_t)(i + 1) * nz + j];
+                double v01 = m[q][(size_t)i * nz + j + 1], v11 = m[q][(size_t)(i + 1) * nz + j + 1];
+                cells[2 * ((size_t)i * (nz - 1) + j) + q] =
+                    make_float4((float)v00, (float)(v10 - v00), (float)(v01 - v00), (float)(v11 - v10 - v01 + v00));
+            }
+        }
+    cudaError_t e;
+    if ((e = dalloc(c->d_cells, cells.size())) != cudaSuccess)
+        return fail(c, CDC_ERR_NOMEM, std::string("field allocation: ") + cudaGetErrorString(e));
+    if ((e = cudaMemcpy(c->d_cells, cells.data(), cells.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "field upload");
+    DevField F{};
+    F.kind = 1;
+    F.B0 = b0;
+    F.cells = c->d_cells;
+    F.nr = nr;
+    F.nz = nz;
+    F.r_min = r_min;
+    F.z_min = z_min;
+    F.inv_dr = 1.0f / dr;
+    F.inv_dz = 1.0f / dz;
+    F.r_max = r_min + dr * (float)(nr - 1);
+    F.z_max = z_min + dz * (float)(nz - 1);
+    F.dr = dr;
+    F.dz = dz;
+    c->F = F;
+    c->field = true;
+    return CDC_OK;
+}
+
+int cdc_reserve(cdc_ctx* c, int max_events, int64_t max_seeds, int64_t max_hits) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom) return fail(c, CDC_ERR_NOT_LOADED, "load the geometry before cdc_reserve");
+    if (max_events < 1 || max_seeds < 0 || max_hits < 0) return fail(c, CDC_ERR_ARG, "reserve sizes");
+    if (max_events > (1 << 20)) return fail(c, CDC_ERR_RANGE, "max_events above 2^20");
+    DeviceGuard g(c->device);
+    free_workspace(c->W);
+    Workspace W;
+    W.max_events = max_events;
+    W.n_wires = c->G.n_wires;
+    W.e_cap = std::max<long long>(max_seeds, (long long)max_events * CDC_MAX_ZOOM * ZOOM_GRID);
+    W.seg_cap = W.e_cap / SEG + max_events + 1;
+    cudaError_t e = cudaSuccess;
+    if ((e = dalloc(W.drift_tab, (size_t)max_events * W.n_wires)) != cudaSuccess ||
+        (e = dalloc(W.E, (size_t)W.e_cap)) != cudaSuccess || (e = dalloc(W.seed_off, (size_t)max_events + 1)) != cudaSuccess ||
+        (e = dalloc(W.seg_off, (size_t)max_events + 1)) != cudaSuccess || (e = dalloc(W.counters, 4)) != cudaSuccess ||
+        (e = dalloc(W.seg_keys, (size_t)W.seg_cap * CDC_MAX_K)) != cudaSuccess ||
+        (e = dalloc(W.round_keys, (size_t)2 * max_events * CDC_MAX_K)) != cudaSuccess ||
+        (e = dalloc(W.best_keys, (size_t)max_events * CDC_MAX_K)) != cudaSuccess ||
+        (e = dalloc(W.zgrids, (size_t)2 * max_events * CDC_MAX_ZOOM)) != cudaSuccess) {
+        free_workspace(W);
+        return fail(c, CDC_ERR_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    }
+    c->W = W;
+    return CDC_OK;
+}
+
+int cdc_hough_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32_t* wire_id,
+                    const cdc_hough_params* p, int32_t* acc, cdc_candidate* cand, int32_t* n_cand, cdc_grid* grid_out,
+                    uint32_t* flags, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom) return fail(c, CDC_ERR_NOT_LOADED, "geometry not loaded");
+    if (n_events < 0) return fail(c, CDC_ERR_ARG, "n_events < 0");
+    if (n_events == 0) return CDC_OK;
+    if (n_events > 65535) return fail(c, CDC_ERR_RANGE, "more than 65535 events per Hough call");
+    if (!p || !hit_off || !wire_id || !acc || !cand || !n_cand || !flags)
+        return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (p->n_bins < 3 || p->n_bins > 4096 || p->bin_um < 2 || (p->bin_um & 1) || p->n_r < 1 || p->n_r > 256 ||
+        p->n_phi < 1 || p->n_phi > 8192 || p->r_min_um < 0 || p->r_step_um < 0 || p->target_um < 0 ||
+        p->min_peak < 1 || p->max_cand < 1 || p->max_cand > 64 || p->r_hist_half_um < 0)
+        return fail(c, CDC_ERR_RANGE, "Hough parameters out of range");
+    if ((long long)p->n_bins * p->bin_um >= (1ll << 30) || llabs((long long)p->origin_um) >= (1ll << 29) ||
+        (long long)p->r_min_um + (long long)p->n_r * p->r_step_um >= (1ll << 29))
+        return fail(c, CDC_ERR_RANGE, "Hough coordinates beyond 2^29 um");
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // integer vote offsets round(R_j (cos, sin)(2 pi k / n_phi)) [um], uploaded once per parameter set
+    const int key[4] = {p->n_r, p->r_min_um, p->r_step_um, p->n_phi};
+    if (memcmp(key, c->off_key, sizeof key) != 0) {
+        const size_t n = (size_t)p->n_r * p->n_phi;
+        std::vector<int2> off(n);
+        for (int j = 0; j < p->n_r; ++j) {
+            const long long R = (long long)p->r_min_um + (long long)j * p->r_step_um;
+            for (int k = 0; k < p->n_phi; ++k) {
+                const double ph = 2.0 * PI * (double)k / (double)p->n_phi;
+                off[(size_t)j * p->n_phi + k] = make_int2((int)llround((double)R * cos(ph)), (int)llround((double)R * sin(ph)));
+            }
+        }
+        if (n > c->offsets_cap) {
+            cudaError_t e = dalloc(c->d_offsets, n);
+            if (e != cudaSuccess) return fail(c, CDC_ERR_NOMEM, "Hough offset table allocation");
+            c->offsets_cap = n;
+        }
+        cudaError_t e = cudaMemcpy(c->d_offsets, off.data(), n * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "Hough offset upload");
+        memcpy(c->off_key, key, sizeof key);
+    }
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_events, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flags reset");
+    HoughLaunch L{n_events, hit_off, wire_id, c->d_offsets, acc, cand, n_cand, grid_out, flags};
+    e = launch_hough(c->G, *p, L, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Hough launch");
+    return CDC_OK;
+}
+
+int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32_t* wire_id, const float* drift,
+                   const cdc_grid* grids, const cdc_scan_params* p, float* E, uint64_t* topk0, float* best_E,
+                   float* best_seed, int8_t* hit_part, float* hit_res2, cdc_grid* zoom_grids, uint32_t* flags,
+                   unsigned long long* steps, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (n_events < 0) return fail(c, CDC_ERR_ARG, "n_events < 0");
+    if (n_events == 0) return CDC_OK;
+    int rc = check_scan_params(c, p, true);
+    if (rc) return rc;
+    if (!hit_off || !wire_id || !drift || !grids || !best_E || !best_seed || !flags)
+        return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (n_events > c->W.max_events || c->W.n_wires < c->G.n_wires)
+        return fail(c, CDC_ERR_NOT_LOADED, "workspace too small: call cdc_reserve");
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_events, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flags reset");
+    ScanLaunch L{n_events, hit_off, wire_id, drift, grids, E, topk0, best_E, best_seed, hit_part, hit_res2, zoom_grids,
+                 flags, steps, p->n_rounds, p->n_rounds > 1 ? p->n_zoom : 1};
+    e = launch_scan(c->G, c->F, make_const(c, p), c->W, L, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scan launch");
+    return CDC_OK;
+}
+
+int cdc_refine_seeds(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, const int32_t* hit_off,
+                     const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
+                     const cdc_refine_params* params, float* seeds_out, double* chi2, float* grad, int32_t* n_used,
+                     uint32_t* flags, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    (void)n_seeds; (void)seed_event; (void)seeds; (void)hit_off; (void)wire_id; (void)drift; (void)scan;
+    (void)params; (void)seeds_out; (void)chi2; (void)grad; (void)n_used; (void)flags; (void)stream;
+    return fail(c, CDC_ERR_RANGE, "refine: not built yet");
+}
+
+int cdc_chi2_grad(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, const int32_t* hit_off,
+                  const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
+                  const cdc_refine_params* params, double* chi2, float* grad, int32_t* n_used, uint32_t* flags,
+                  void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    (void)n_seeds; (void)seed_event; (void)seeds; (void)hit_off; (void)wire_id; (void)drift; (void)scan;
+    (void)params; (void)chi2; (void)grad; (void)n_used; (void)flags; (void)stream;
+    return fail(c, CDC_ERR_RANGE, "chi2_grad: not built yet");
+}
+
+int cdc_propagate(cdc_ctx* c, int n_seeds, const float* seeds, const cdc_scan_params* p, int every, int n_rec,
+                  int precision, double* pos, int32_t* n_steps, double* path, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (n_seeds < 0) return fail(c, CDC_ERR_ARG, "n_seeds < 0");
+    if (n_seeds == 0) return CDC_OK;
+    int rc = check_scan_params(c, p, false);
+    if (rc) return rc;
+    if (!seeds || !pos || !n_steps || !path) return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (every < 1 || n_rec < 1) return fail(c, CDC_ERR_ARG, "every and n_rec must be >= 1");
+    if (precision != 0 && precision != 1) return fail(c, CDC_ERR_ARG, "precision must be 0 or 1");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_propagate(c->G, c->F, make_const(c, p), n_seeds, seeds, every, n_rec, precision, pos,
+                                     n_steps, path, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
+    return CDC_OK;
+}
+
+}  // extern "C"

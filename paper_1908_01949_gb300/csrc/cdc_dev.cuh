@@ -1,0 +1,211 @@
+// Device-side data layout and helpers shared by the CUDA translation units of
+// the seed-scanning track finder (arXiv:1908.01949).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cdc.h"
+
+namespace cdc {
+
+constexpr float KAPPA = 0.299792458f;      // MeV/c per (T mm)
+constexpr double KAPPA_D = 0.299792458;
+constexpr int TAB_N = 1024;                // radial candidate-layer table, 1 mm bins
+constexpr float TAB_BAND = 24.0f;          // widest layer band the table supports [mm]
+constexpr int SEG = 4096;                  // seeds per top-K segment
+constexpr uint64_t KEY_NONE = ~0ull;       // empty top-K slot
+constexpr int ZOOM_GRID = 243;             // 3^5 seeds per zoom grid
+constexpr int ROUND_SHIFT = 27;            // best-list key: (round << 27) | index
+
+// One sense layer, as the kernels read it from shared memory.
+struct DevLayer {
+    float R2;            // waist radius squared [mm^2]
+    float tan2a;         // tan^2(alpha)
+    float tana_over_R;   // tan(alpha) / R: tangent of the stereo twist per mm of z
+    float phi_off;       // azimuth of wire 0 [rad]
+    float n_over_2pi;    // N / (2 pi): cells per radian
+    float cells_per_mm;  // N / (2 pi (R - TAB_BAND)): conservative cells per mm of arc
+    float cosa;          // cos(alpha): z component of the wire direction
+    float pad;
+    int N;               // wires in the layer
+    int base;            // global id of wire 0
+    int pad2, pad3;
+};
+
+// Geometry tables owned by the context (device memory).
+struct DevGeom {
+    const DevLayer* layers;  // [n_layers]
+    const float4* wires;     // [n_wires]: (mx, my, dx, dy) of the wire line (m at z = 0; dz = layer cosa)
+    const uchar2* tab;       // [TAB_N]: (first, last) layer whose band may contain rho in [b, b+1) mm
+    const int2* wire_um;     // [n_wires]: wire (x, y) at z = 0 rounded to um (Hough input)
+    int n_layers, n_wires;
+    float z_half, R0, R_out;
+    double R0d;
+};
+
+// Field: uniform Bz or bilinear (r, z) map stored as per-cell coefficients.
+struct DevField {
+    int kind;                // 0 uniform, 1 map
+    float B0;
+    const float4* cells;     // [(nr-1)(nz-1)][2]: Bz and Br as a + b u + c v + d u v per cell
+    int nr, nz;
+    float r_min, z_min, inv_dr, inv_dz, r_max, z_max;
+    double dr, dz;
+};
+
+// Scan-call parameters, resolved on the host.
+struct ScanConst {
+    float h, lam, charge_dir, band, d_win, max_drift;
+    int max_steps, max_part, direction, k;
+};
+
+// ------------------------------------------------------------------ field
+template <int KIND>
+__device__ __forceinline__ void field_eval(const DevField& F, float x, float y, float z, float& bx, float& by,
+                                           float& bz) {
+    if (KIND == 0) {
+        bx = 0.f;
+        by = 0.f;
+        bz = F.B0;
+    } else {
+        float r2 = fmaf(x, x, y * y);
+        float rho = sqrtf(r2);
+        float rinv = rho > 0.f ? 1.0f / rho : 0.f;
+        float rc = fminf(fmaxf(rho, F.r_min), F.r_max);
+        float zc = fminf(fmaxf(z, F.z_min), F.z_max);
+        float u = (rc - F.r_min) * F.inv_dr;
+        float v = (zc - F.z_min) * F.inv_dz;
+        int i = min((int)u, F.nr - 2);
+        int j = min((int)v, F.nz - 2);
+        u -= (float)i;
+        v -= (float)j;
+        const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
+        float4 cz = __ldg(c);
+        float4 cr = __ldg(c + 1);
+        bz = fmaf(v, fmaf(cz.w, u, cz.z), fmaf(cz.y, u, cz.x));
+        float br = fmaf(v, fmaf(cr.w, u, cr.z), fmaf(cr.y, u, cr.x));
+        float s = br * rinv;
+        bx = s * x;
+        by = s * y;
+    }
+}
+
+// --------------------------------------------------------- FP32 stepper
+// Track state: position and unit direction as unevaluated float sums
+// (hi + lo, Kahan-compensated updates) and lam = q kappa / p.
+struct State {
+    float rx, ry, rz, lx, ly, lz;  // position hi / lo
+    float tx, ty, tz, mx, my, mz;  // direction hi / lo
+    float lam;
+};
+
+__device__ __forceinline__ void kahan(float& hi, float& lo, float inc) {
+    float y = inc + lo;
+    float s = hi + y;
+    lo = y - (s - hi);
+    hi = s;
+}
+
+__device__ __forceinline__ void cross_lam(float lam, float ax, float ay, float az, float bx, float by, float bz,
+                                          float& cx, float& cy, float& cz) {
+    cx = lam * fmaf(ay, bz, -az * by);
+    cy = lam * fmaf(az, bx, -ax * bz);
+    cz = lam * fmaf(ax, by, -ay * bx);
+}
+
+// One classical Runge-Kutta-Nystrom step of length h (Abramowitz & Stegun
+// 25.5.20) for r'' = lam (r' x B(r)): field at the start, at the midpoint
+// r + h/2 t + h^2/8 k1 (shared by k2 and k3) and at r + h t + h^2/2 k3.  The
+// increments are formed in FP32 and added to the compensated state.
+template <int KIND>
+__device__ __forceinline__ void rkn_step(const DevField& F, State& s, float h) {
+    const float h2 = 0.5f * h, hh8 = h * h * 0.125f, hh2 = h * h * 0.5f, hh6 = h * h * (1.0f / 6.0f),
+                h6 = h * (1.0f / 6.0f);
+    float bx, by, bz;
+    float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+    field_eval<KIND>(F, s.rx, s.ry, s.rz, bx, by, bz);
+    cross_lam(s.lam, s.tx, s.ty, s.tz, bx, by, bz, k1x, k1y, k1z);
+    float px = fmaf(hh8, k1x, fmaf(h2, s.tx, s.rx));
+    float py = fmaf(hh8, k1y, fmaf(h2, s.ty, s.ry));
+    float pz = fmaf(hh8, k1z, fmaf(h2, s.tz, s.rz));
+    if (KIND != 0) field_eval<KIND>(F, px, py, pz, bx, by, bz);
+    cross_lam(s.lam, fmaf(h2, k1x, s.tx), fmaf(h2, k1y, s.ty), fmaf(h2, k1z, s.tz), bx, by, bz, k2x, k2y, k2z);
+    cross_lam(s.lam, fmaf(h2, k2x, s.tx), fmaf(h2, k2y, s.ty), fmaf(h2, k2z, s.tz), bx, by, bz, k3x, k3y, k3z);
+    if (KIND != 0) {
+        px = fmaf(hh2, k3x, fmaf(h, s.tx, s.rx));
+        py = fmaf(hh2, k3y, fmaf(h, s.ty, s.ry));
+        pz = fmaf(hh2, k3z, fmaf(h, s.tz, s.rz));
+        field_eval<KIND>(F, px, py, pz, bx, by, bz);
+    }
+    cross_lam(s.lam, fmaf(h, k3x, s.tx), fmaf(h, k3y, s.ty), fmaf(h, k3z, s.tz), bx, by, bz, k4x, k4y, k4z);
+    // position: h (t_hi + t_lo) + h^2/6 (k1 + k2 + k3)
+    float drx = fmaf(h, s.tx, fmaf(h, s.mx, hh6 * (k1x + k2x + k3x)));
+    float dry = fmaf(h, s.ty, fmaf(h, s.my, hh6 * (k1y + k2y + k3y)));
+    float drz = fmaf(h, s.tz, fmaf(h, s.mz, hh6 * (k1z + k2z + k3z)));
+    // direction: h/6 (k1 + 2 k2 + 2 k3 + k4)
+    float dtx = h6 * (k1x + k4x + 2.0f * (k2x + k3x));
+    float dty = h6 * (k1y + k4y + 2.0f * (k2y + k3y));
+    float dtz = h6 * (k1z + k4z + 2.0f * (k2z + k3z));
+    kahan(s.rx, s.lx, drx);
+    kahan(s.ry, s.ly, dry);
+    kahan(s.rz, s.lz, drz);
+    kahan(s.tx, s.mx, dtx);
+    kahan(s.ty, s.my, dty);
+    kahan(s.tz, s.mz, dtz);
+}
+
+// Seed (theta0, z0, px0, py0, pz0) at r = R0 -> state, formed in FP64 and
+// split into hi/lo floats.  direction -1 reverses t and the charge.
+__device__ __forceinline__ void seed_state(const float* sd, double R0, float charge_dir, int direction, State& s) {
+    double st, ct;
+    sincos((double)sd[0], &st, &ct);
+    double x = R0 * ct, y = R0 * st, z = (double)sd[1];
+    double px = sd[2], py = sd[3], pz = sd[4];
+    double p = sqrt(px * px + py * py + pz * pz);
+    double ip = (direction < 0 ? -1.0 : 1.0) / p;
+    double tx = px * ip, ty = py * ip, tz = pz * ip;
+    s.rx = (float)x;
+    s.lx = (float)(x - (double)s.rx);
+    s.ry = (float)y;
+    s.ly = (float)(y - (double)s.ry);
+    s.rz = (float)z;
+    s.lz = (float)(z - (double)s.rz);
+    s.tx = (float)tx;
+    s.mx = (float)(tx - (double)s.tx);
+    s.ty = (float)ty;
+    s.my = (float)(ty - (double)s.ty);
+    s.tz = (float)tz;
+    s.mz = (float)(tz - (double)s.tz);
+    s.lam = (float)((double)charge_dir * KAPPA_D / p);
+}
+
+// Mixed-radix decode of seed `idx` of one grid (row-major over theta0, z0,
+// px0, py0, pz0); each value is the float32 nearest centre + k step.
+__device__ __forceinline__ void grid_seed(const cdc_grid& g, long long idx, float* out) {
+    long long q = idx;
+    int ia[5];
+#pragma unroll
+    for (int a = 4; a >= 0; --a) {
+        int n = g.n[a];
+        ia[a] = (int)(q % n);
+        q /= n;
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) out[a] = fmaf((float)ia[a] - 0.5f * (float)(g.n[a] - 1), g.step[a], g.centre[a]);
+}
+
+__device__ __forceinline__ long long grid_count(const cdc_grid& g) {
+    long long c = 1;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) c *= (long long)max(g.n[a], 0);
+    return c;
+}
+
+__device__ __forceinline__ uint64_t make_key(float e, uint32_t idx) {
+    uint32_t b = __float_as_uint(e);
+    if (!(e >= 0.f)) b = 0x7f800000u;  // NaN or negative cannot occur; order them last
+    return ((uint64_t)b << 32) | idx;
+}
+
+}  // namespace cdc

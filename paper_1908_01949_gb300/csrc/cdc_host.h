@@ -1,0 +1,87 @@
+// Host-side declarations shared by the C-ABI layer and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cdc_dev.cuh"
+
+namespace cdc {
+
+// Device workspace owned by a context, sized by cdc_reserve.
+struct Workspace {
+    float* drift_tab = nullptr;            // [max_events][n_wires]: drift of the fired wire, sentinel if none
+    float* E = nullptr;                    // [e_cap] scores of the current round
+    long long* seed_off = nullptr;         // [max_events + 1]
+    int* seg_off = nullptr;                // [max_events + 1]
+    unsigned long long* counters = nullptr;// [4]: work counter, total seeds, total segments, spare
+    uint64_t* seg_keys = nullptr;          // [seg_cap][CDC_MAX_K]
+    uint64_t* round_keys = nullptr;        // [2][max_events][CDC_MAX_K]
+    uint64_t* best_keys = nullptr;         // [max_events][CDC_MAX_K]
+    cdc_grid* zgrids = nullptr;            // [2][max_events][CDC_MAX_ZOOM]
+    int max_events = 0;
+    long long e_cap = 0, seg_cap = 0;
+    int n_wires = 0;
+};
+
+struct ScanLaunch {
+    int n_events;
+    const int32_t* hit_off;
+    const int32_t* wire_id;
+    const float* drift;
+    const cdc_grid* grids0;   // caller's coarse grids, one per event
+    float* E0;                // caller's coarse-round E output or nullptr
+    uint64_t* topk0;
+    float* best_E;
+    float* best_seed;
+    int8_t* hit_part;
+    float* hit_res2;
+    cdc_grid* zoom_grids;
+    uint32_t* flags;
+    unsigned long long* steps;
+    int n_rounds, n_zoom;
+};
+
+// Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
+                        const ScanLaunch& L, int num_sms, cudaStream_t st);
+
+cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
+                             const float* seeds, int every, int n_rec, int precision, double* pos, int32_t* n_steps,
+                             double* path, cudaStream_t st);
+
+// Hough (hough.cu).
+struct HoughLaunch {
+    int n_events;
+    const int32_t* hit_off;
+    const int32_t* wire_id;
+    const int2* offsets;       // [n_r * n_phi] integer (dx, dy) of each vote [um]
+    int32_t* acc;
+    cdc_candidate* cand;
+    int32_t* n_cand;
+    cdc_grid* grid_out;
+    uint32_t* flags;
+};
+cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const HoughLaunch& L, cudaStream_t st);
+
+// Refine (refine.cu).
+struct RefineLaunch {
+    int n_seeds;
+    const int32_t* seed_event;
+    const float* seeds;
+    const int32_t* hit_off;
+    const int32_t* wire_id;
+    const float* drift;
+    int n_iter;
+    float sigma;
+    float scale[5];
+    int checkpoint;
+    float* seeds_out;
+    double* chi2;
+    float* grad;
+    int32_t* n_used;
+    uint32_t* flags;
+};
+cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& P, const RefineLaunch& L,
+                          cudaStream_t st);
+
+}  // namespace cdc

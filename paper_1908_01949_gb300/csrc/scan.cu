@@ -1,0 +1,610 @@
+// Seed scan kernels (arXiv:1908.01949 sec. 2.2, Eq. 1): hit staging, the
+// persistent thread-per-seed RKN scorer, warp-level top-K, the zoom re-scan
+// grids and the hit-to-turn classification of the best seed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cdc_dev.cuh"
+#include "cdc_host.h"
+#include "tracer.cuh"
+
+namespace cdc {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float NOT_FIRED = 3.0e38f;   // drift-table sentinel (above any valid drift)
+
+// ---------------------------------------------------------------- staging
+// drift_tab[e][wire] = drift of the event's hit on that wire; validates the
+// wire id and drift range; duplicate wires keep the smaller drift and flag.
+__global__ void stage_kernel(int n_events, const int32_t* __restrict__ hit_off, const int32_t* __restrict__ wire_id,
+                             const float* __restrict__ drift, int n_wires, float max_drift, float* drift_tab,
+                             uint32_t* flags) {
+    const int total = hit_off[n_events];
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < total; h += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_events - 1;
+        while (lo < hi) {  // event e with hit_off[e] <= h < hit_off[e+1]
+            int mid = (lo + hi + 1) >> 1;
+            if (hit_off[mid] <= h) lo = mid; else hi = mid - 1;
+        }
+        int w = wire_id[h];
+        float d = drift[h];
+        if (w < 0 || w >= n_wires || !(d >= 0.f && d <= max_drift)) {
+            atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
+            continue;
+        }
+        int old = atomicMin((int*)&drift_tab[(size_t)lo * n_wires + w], __float_as_int(d));
+        if (old != __float_as_int(NOT_FIRED)) atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
+    }
+}
+
+__global__ void fill_kernel(float* p, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// --------------------------------------------------------------- prologue
+// Seed and top-K segment offsets of every event for one round; resets the
+// work counter.  One block.
+__global__ void prologue_kernel(int n_events, const cdc_grid* __restrict__ grids, int gpe, long long cap,
+                                long long seg_cap, long long* seed_off, int* seg_off, unsigned long long* counters,
+                                uint32_t* flags) {
+    __shared__ long long s_sum[1024];
+    __shared__ int s_seg[1024];
+    __shared__ long long s_base;
+    __shared__ int s_sbase;
+    if (threadIdx.x == 0) {
+        s_base = 0;
+        s_sbase = 0;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < n_events; c0 += blockDim.x) {
+        int e = c0 + threadIdx.x;
+        long long n = 0;
+        if (e < n_events) {
+            for (int g = 0; g < gpe; ++g) n += grid_count(grids[(size_t)e * gpe + g]);
+            if (n >= (1ll << ROUND_SHIFT)) {
+                atomicOr(&flags[e], CDC_FLAG_EMPTY);
+                n = 0;
+            }
+        }
+        int sg = (int)((n + SEG - 1) / SEG);
+        s_sum[threadIdx.x] = n;
+        s_seg[threadIdx.x] = sg;
+        __syncthreads();
+        for (int off = 1; off < blockDim.x; off <<= 1) {  // inclusive scan
+            long long a = threadIdx.x >= off ? s_sum[threadIdx.x - off] : 0;
+            int b = threadIdx.x >= off ? s_seg[threadIdx.x - off] : 0;
+            __syncthreads();
+            s_sum[threadIdx.x] += a;
+            s_seg[threadIdx.x] += b;
+            __syncthreads();
+        }
+        if (e < n_events) {
+            seed_off[e] = s_base + s_sum[threadIdx.x] - n;
+            seg_off[e] = s_sbase + s_seg[threadIdx.x] - sg;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) {
+            s_base += s_sum[threadIdx.x];
+            s_sbase += s_seg[threadIdx.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long tot = s_base;
+        if (tot > cap || (long long)s_sbase > seg_cap) {  // beyond the buffers: scan nothing, flag every event
+            for (int e = 0; e < n_events; ++e) atomicOr(&flags[e], CDC_FLAG_EMPTY);
+            tot = 0;
+        }
+        seed_off[n_events] = tot;
+        seg_off[n_events] = tot ? s_sbase : 0;
+        counters[0] = 0;
+        counters[1] = (unsigned long long)tot;
+        counters[2] = (unsigned long long)(tot ? s_sbase : 0);
+    }
+}
+
+__device__ __forceinline__ int find_event(const long long* off, int n, long long i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void event_seed(const cdc_grid* grids, int gpe, int e, long long local, float* sd) {
+    for (int g = 0; g < gpe; ++g) {
+        const cdc_grid& gr = grids[(size_t)e * gpe + g];
+        long long c = grid_count(gr);
+        if (local < c || g == gpe - 1) {
+            grid_seed(gr, local, sd);
+            return;
+        }
+        local -= c;
+    }
+}
+
+// ------------------------------------------------------------- the scan
+struct ScanIO {
+    const float* drift_tab;
+    const int32_t* hit_off;
+    const cdc_grid* grids;
+    int gpe;
+    const long long* seed_off;
+    int n_events;
+    unsigned long long* counters;
+    float* E;
+    uint32_t* flags;
+    unsigned long long* steps;
+};
+
+// Persistent thread-per-seed scorer.  Each lane takes seeds from a global
+// counter (warp-aggregated atomics) and steps its seed in chunks of 16 RKN
+// steps; a lane whose seed ended takes a new one at the next chunk boundary,
+// so lanes stay busy although seeds end after very different step counts.
+template <int KIND>
+__global__ void __launch_bounds__(256) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+    __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
+    __shared__ uchar2 s_tab[TAB_N];
+    for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
+    for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
+    __syncthreads();
+    const long long total = (long long)io.counters[1];
+    const int lane = threadIdx.x & 31;
+    Tracer<KIND, false> T;
+    long long my = -1;  // -1: wants a seed, -2: no seeds left
+    int ev = 0;
+    unsigned long long nsteps = 0;
+    for (;;) {
+        unsigned need = __ballot_sync(FULL, my == -1);
+        if (need) {
+            int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&io.counters[0], (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (my == -1) {
+                long long s = (long long)base + __popc(need & ((1u << lane) - 1u));
+                if (s < total) {
+                    my = s;
+                    ev = find_event(io.seed_off, io.n_events, s);
+                    float sd[5];
+                    event_seed(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
+                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * G.n_wires, sd);
+                } else {
+                    my = -2;
+                }
+            }
+        }
+        if (__all_sync(FULL, my == -2)) break;
+        if (my >= 0) {
+            for (int it = 0; it < 16; ++it) {
+                if (!T.step(G, F, P, s_lay, s_tab)) {
+                    int H = io.hit_off[ev + 1] - io.hit_off[ev];
+                    io.E[my] = T.score(P, H);
+                    if (T.flags) atomicOr(&io.flags[ev], T.flags);
+                    nsteps += (unsigned long long)T.n;
+                    my = -1;
+                    break;
+                }
+            }
+        }
+    }
+    if (io.steps) {
+        for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_down_sync(FULL, nsteps, o);
+        if (lane == 0 && nsteps) atomicAdd(io.steps, nsteps);
+    }
+}
+
+// ------------------------------------------------------------------ top-K
+// Warp-resident sorted list of up to 64 keys: lane l holds entries l and 32+l.
+__device__ __forceinline__ uint64_t list_at(uint64_t a, uint64_t b, int i) {
+    uint64_t va = __shfl_sync(FULL, a, i & 31);
+    uint64_t vb = __shfl_sync(FULL, b, i & 31);
+    return i < 32 ? va : vb;
+}
+
+__device__ __forceinline__ void list_insert(uint64_t& a, uint64_t& b, uint64_t key, bool cand, int K) {
+    const int lane = threadIdx.x & 31;
+    uint64_t thr = list_at(a, b, K - 1);
+    unsigned m = __ballot_sync(FULL, cand && key < thr);
+    while (m) {
+        int src = __ffs(m) - 1;
+        uint64_t k = __shfl_sync(FULL, key, src);
+        int p = __popc(__ballot_sync(FULL, a < k)) + __popc(__ballot_sync(FULL, b < k));
+        uint64_t pa = __shfl_up_sync(FULL, a, 1);
+        uint64_t pb = __shfl_up_sync(FULL, b, 1);
+        uint64_t a31 = __shfl_sync(FULL, a, 31);
+        if (lane == 0) pb = a31;
+        int ia = lane, ib = 32 + lane;
+        uint64_t na = ia < p ? a : (ia == p ? k : pa);
+        uint64_t nb = ib < p ? b : (ib == p ? k : pb);
+        a = na;
+        b = nb;
+        thr = list_at(a, b, K - 1);
+        m &= ~(1u << src);
+        m &= __ballot_sync(FULL, cand && key < thr);
+    }
+}
+
+// One warp per segment of SEG seeds: the K lowest (E, index) keys.
+__global__ void topk_partial_kernel(const float* __restrict__ E, const long long* __restrict__ seed_off,
+                                    const int* __restrict__ seg_off, int n_events,
+                                    const unsigned long long* counters, int K, uint64_t* seg_keys) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const long long n_seg = (long long)counters[2];
+    for (long long s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_seg; s += warps) {
+        int lo = 0, hi = n_events - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (seg_off[mid] <= s) lo = mid; else hi = mid - 1;
+        }
+        const int e = lo;
+        const long long n_e = seed_off[e + 1] - seed_off[e];
+        const long long a0 = (s - seg_off[e]) * (long long)SEG;
+        const long long a1 = min(a0 + SEG, n_e);
+        uint64_t la = KEY_NONE, lb = KEY_NONE;
+        for (long long i0 = a0; i0 < a1; i0 += 32) {
+            long long i = i0 + lane;
+            bool ok = i < a1;
+            uint64_t key = ok ? make_key(E[seed_off[e] + i], (uint32_t)i) : KEY_NONE;
+            list_insert(la, lb, key, ok, K);
+        }
+        uint64_t* out = seg_keys + s * CDC_MAX_K;
+        if (lane < K) out[lane] = la;
+        if (32 + lane < K) out[32 + lane] = lb;
+    }
+}
+
+// One warp per event: merge the segment lists into the round's top-K.
+__global__ void topk_merge_kernel(const int* __restrict__ seg_off, int n_events, int K,
+                                  const uint64_t* __restrict__ seg_keys, uint64_t* round_keys) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= n_events) return;
+    uint64_t la = KEY_NONE, lb = KEY_NONE;
+    const long long total = (long long)(seg_off[e + 1] - seg_off[e]) * K;
+    const uint64_t* src = seg_keys + (long long)seg_off[e] * CDC_MAX_K;
+    for (long long i0 = 0; i0 < total; i0 += 32) {
+        long long i = i0 + lane;
+        bool ok = i < total;
+        uint64_t key = ok ? src[(i / K) * CDC_MAX_K + (i % K)] : KEY_NONE;
+        list_insert(la, lb, key, ok && key != KEY_NONE, K);
+    }
+    uint64_t* out = round_keys + (size_t)e * CDC_MAX_K;
+    if (lane < K) out[lane] = la;
+    if (32 + lane < K) out[32 + lane] = lb;
+}
+
+// One thread per event: merge round r's top-K into the best list over all
+// rounds, ordered by (E, round, index); seeds decoded from round r's grids.
+__global__ void merge_best_kernel(int n_events, int K, int round, const uint64_t* __restrict__ round_keys,
+                                  const cdc_grid* __restrict__ grids, int gpe, uint64_t* best_keys, float* best_E,
+                                  float* best_seed, uint64_t* topk0) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_events) return;
+    uint64_t ok[CDC_MAX_K];
+    float os[CDC_MAX_K][5];
+    const uint64_t* rk = round_keys + (size_t)e * CDC_MAX_K;
+    uint64_t* bk = best_keys + (size_t)e * CDC_MAX_K;
+    for (int i = 0; i < K; ++i) {
+        ok[i] = round == 0 ? KEY_NONE : bk[i];
+        for (int a = 0; a < 5; ++a) os[i][a] = round == 0 ? 0.f : best_seed[((size_t)e * K + i) * 5 + a];
+    }
+    if (round == 0 && topk0)
+        for (int i = 0; i < K; ++i) topk0[(size_t)e * K + i] = rk[i];
+    int p = 0, q = 0;
+    for (int i = 0; i < K; ++i) {
+        uint64_t nk = rk[q] == KEY_NONE ? KEY_NONE
+                                        : ((rk[q] & 0xffffffff00000000ull) | ((uint64_t)round << ROUND_SHIFT) |
+                                           (rk[q] & ((1ull << ROUND_SHIFT) - 1)));
+        bool take_new = (q < K) && nk < ok[p];
+        uint64_t key;
+        float sd[5];
+        if (take_new) {
+            key = nk;
+            event_seed(grids, gpe, e, (long long)(rk[q] & 0xffffffffull), sd);
+            ++q;
+        } else {
+            key = ok[p];
+            for (int a = 0; a < 5; ++a) sd[a] = os[p][a];
+            ++p;
+        }
+        bk[i] = key;
+        best_E[(size_t)e * K + i] = key == KEY_NONE ? __int_as_float(0x7f800000) : __uint_as_float((uint32_t)(key >> 32));
+        for (int a = 0; a < 5; ++a)
+            best_seed[((size_t)e * K + i) * 5 + a] = key == KEY_NONE ? __int_as_float(0x7fffffff) : sd[a];
+    }
+}
+
+// Zoom grids of round r (sec. 2.2: finer seed sets around the candidates):
+// around each of the previous round's n_zoom best seeds a 3^5 grid with the
+// coarse step times 2^-r.
+__global__ void zoom_grid_kernel(int n_events, int n_zoom, int round, const uint64_t* __restrict__ prev_keys,
+                                 const cdc_grid* __restrict__ prev_grids, int prev_gpe,
+                                 const cdc_grid* __restrict__ grids0, cdc_grid* out, cdc_grid* record) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_events * n_zoom) return;
+    int e = t / n_zoom, c = t % n_zoom;
+    uint64_t key = prev_keys[(size_t)e * CDC_MAX_K + c];
+    cdc_grid g;
+    float f = ldexpf(1.0f, -round);
+    for (int a = 0; a < 5; ++a) {
+        g.step[a] = grids0[e].step[a] * f;
+        g.n[a] = key == KEY_NONE ? 0 : 3;
+        g.centre[a] = 0.f;
+    }
+    if (key != KEY_NONE) event_seed(prev_grids, prev_gpe, e, (long long)(key & 0xffffffffull), g.centre);
+    out[(size_t)e * CDC_MAX_ZOOM + c] = g;
+    if (record) record[(size_t)e * n_zoom + c] = g;
+}
+
+__global__ void record_round0_kernel(int n_events, int n_zoom, const cdc_grid* grids0, cdc_grid* record) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_events * n_zoom) return;
+    int e = t / n_zoom, c = t % n_zoom;
+    cdc_grid g = grids0[e];
+    if (c > 0)
+        for (int a = 0; a < 5; ++a) g.n[a] = 0;
+    record[(size_t)e * n_zoom + c] = g;
+}
+
+// Hit classification of each event's best seed (sec. 2.2: hits with
+// d^2 < lambda belong to the partition under investigation).
+template <int KIND>
+__global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, ScanConst P, int n_events,
+                                                     const float* __restrict__ drift_tab,
+                                                     const int32_t* __restrict__ hit_off,
+                                                     const int32_t* __restrict__ wire_id,
+                                                     const float* __restrict__ best_seed, int K, int8_t* hit_part,
+                                                     float* hit_res2) {
+    __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
+    __shared__ uchar2 s_tab[TAB_N];
+    for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
+    for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
+    __syncthreads();
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_events) return;
+    float sd[5];
+    bool valid = true;
+    for (int a = 0; a < 5; ++a) {
+        sd[a] = best_seed[(size_t)e * K * 5 + a];
+        valid &= (sd[a] == sd[a]);
+    }
+    const int h0 = hit_off[e], h1 = hit_off[e + 1];
+    if (!valid) {
+        for (int h = h0; h < h1; ++h) {
+            if (hit_part) hit_part[h] = -1;
+            if (hit_res2) hit_res2[h] = P.lam;
+        }
+        return;
+    }
+    Tracer<KIND, true> T;
+    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * G.n_wires, sd);
+    while (T.step(G, F, P, s_lay, s_tab)) {
+    }
+    for (int h = h0; h < h1; ++h) {
+        int w = wire_id[h];
+        int part = -1;
+        float r2 = P.lam;
+        T.lookup(w, part, r2);
+        if (hit_part) hit_part[h] = (int8_t)part;
+        if (hit_res2) hit_res2[h] = r2;
+    }
+}
+
+// ------------------------------------------------------------ propagation
+template <int KIND>
+__global__ void propagate_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds, const float* __restrict__ seeds,
+                                 int every, int n_rec, double* pos, int32_t* n_steps, double* path) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seeds) return;
+    State s;
+    seed_state(seeds + 5 * (size_t)i, G.R0d, P.charge_dir, P.direction, s);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int r = 0; r < n_rec; ++r)
+        for (int a = 0; a < 3; ++a) pos[((size_t)i * n_rec + r) * 3 + a] = nan;
+    int n = 0, part = 0;
+    bool outside = true;
+    for (;;) {
+        if (n >= P.max_steps) break;
+        rkn_step<KIND>(F, s, P.h);
+        ++n;
+        if (n % every == 0 && n / every <= n_rec) {
+            double* o = pos + ((size_t)i * n_rec + (n / every - 1)) * 3;
+            o[0] = (double)s.rx + (double)s.lx;
+            o[1] = (double)s.ry + (double)s.ly;
+            o[2] = (double)s.rz + (double)s.lz;
+        }
+        float rho = sqrtf(fmaf(s.rx, s.rx, s.ry * s.ry));
+        bool now_out = rho >= G.R0;
+        bool stop = false;
+        if (outside && !now_out) {
+            ++part;
+            stop = part >= P.max_part;
+        }
+        outside = now_out;
+        if (fabsf(s.rz) > G.z_half || rho > G.R_out) stop = true;
+        if (stop) break;
+    }
+    n_steps[i] = n;
+    path[i] = (double)n * (double)P.h;  // fixed step: the FP64 path length is the step count times h
+}
+
+// FP64 reference stepper on the GPU (precision sweep).
+template <int KIND>
+__device__ void field_eval_d(const DevField& F, double x, double y, double z, double& bx, double& by, double& bz) {
+    if (KIND == 0) {
+        bx = 0;
+        by = 0;
+        bz = F.B0;
+        return;
+    }
+    double rho = sqrt(x * x + y * y);
+    double rmax = F.r_min + F.dr * (F.nr - 1), zmax = F.z_min + F.dz * (F.nz - 1);
+    double rc = fmin(fmax(rho, (double)F.r_min), rmax), zc = fmin(fmax(z, (double)F.z_min), zmax);
+    double u = (rc - F.r_min) / F.dr, v = (zc - F.z_min) / F.dz;
+    int i = min((int)u, F.nr - 2), j = min((int)v, F.nz - 2);
+    u -= i;
+    v -= j;
+    const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
+    float4 cz = c[0], cr = c[1];
+    bz = (double)cz.x + (double)cz.y * u + (double)cz.z * v + (double)cz.w * u * v;
+    double br = (double)cr.x + (double)cr.y * u + (double)cr.z * v + (double)cr.w * u * v;
+    bx = rho > 0 ? br * x / rho : 0.0;
+    by = rho > 0 ? br * y / rho : 0.0;
+}
+
+template <int KIND>
+__global__ void propagate_fp64_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds, const float* __restrict__ seeds,
+                                      int every, int n_rec, double* pos, int32_t* n_steps, double* path) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seeds) return;
+    const float* sd = seeds + 5 * (size_t)i;
+    double st, ct;
+    sincos((double)sd[0], &st, &ct);
+    double r[3] = {G.R0d * ct, G.R0d * st, (double)sd[1]};
+    double p = sqrt((double)sd[2] * sd[2] + (double)sd[3] * sd[3] + (double)sd[4] * sd[4]);
+    double ip = (P.direction < 0 ? -1.0 : 1.0) / p;
+    double t[3] = {sd[2] * ip, sd[3] * ip, sd[4] * ip};
+    double lam = (double)P.charge_dir * KAPPA_D / p, h = P.h;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int q = 0; q < n_rec; ++q)
+        for (int a = 0; a < 3; ++a) pos[((size_t)i * n_rec + q) * 3 + a] = nan;
+    int n = 0, part = 0;
+    bool outside = true;
+    for (;;) {
+        if (n >= P.max_steps) break;
+        double B[3], k1[3], k2[3], k3[3], k4[3], tt[3], pm[3];
+        field_eval_d<KIND>(F, r[0], r[1], r[2], B[0], B[1], B[2]);
+        k1[0] = lam * (t[1] * B[2] - t[2] * B[1]);
+        k1[1] = lam * (t[2] * B[0] - t[0] * B[2]);
+        k1[2] = lam * (t[0] * B[1] - t[1] * B[0]);
+        for (int a = 0; a < 3; ++a) {
+            pm[a] = r[a] + 0.5 * h * t[a] + h * h / 8.0 * k1[a];
+            tt[a] = t[a] + 0.5 * h * k1[a];
+        }
+        field_eval_d<KIND>(F, pm[0], pm[1], pm[2], B[0], B[1], B[2]);
+        k2[0] = lam * (tt[1] * B[2] - tt[2] * B[1]);
+        k2[1] = lam * (tt[2] * B[0] - tt[0] * B[2]);
+        k2[2] = lam * (tt[0] * B[1] - tt[1] * B[0]);
+        for (int a = 0; a < 3; ++a) tt[a] = t[a] + 0.5 * h * k2[a];
+        k3[0] = lam * (tt[1] * B[2] - tt[2] * B[1]);
+        k3[1] = lam * (tt[2] * B[0] - tt[0] * B[2]);
+        k3[2] = lam * (tt[0] * B[1] - tt[1] * B[0]);
+        for (int a = 0; a < 3; ++a) {
+            pm[a] = r[a] + h * t[a] + 0.5 * h * h * k3[a];
+            tt[a] = t[a] + h * k3[a];
+        }
+        field_eval_d<KIND>(F, pm[0], pm[1], pm[2], B[0], B[1], B[2]);
+        k4[0] = lam * (tt[1] * B[2] - tt[2] * B[1]);
+        k4[1] = lam * (tt[2] * B[0] - tt[0] * B[2]);
+        k4[2] = lam * (tt[0] * B[1] - tt[1] * B[0]);
+        for (int a = 0; a < 3; ++a) {
+            r[a] += h * t[a] + h * h / 6.0 * (k1[a] + k2[a] + k3[a]);
+            t[a] += h / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+        }
+        ++n;
+        if (n % every == 0 && n / every <= n_rec) {
+            double* o = pos + ((size_t)i * n_rec + (n / every - 1)) * 3;
+            o[0] = r[0];
+            o[1] = r[1];
+            o[2] = r[2];
+        }
+        double rho = sqrt(r[0] * r[0] + r[1] * r[1]);
+        bool now_out = rho >= G.R0d;
+        bool stop = false;
+        if (outside && !now_out) {
+            ++part;
+            stop = part >= P.max_part;
+        }
+        outside = now_out;
+        if (fabs(r[2]) > (double)G.z_half || rho > (double)G.R_out) stop = true;
+        if (stop) break;
+    }
+    n_steps[i] = n;
+    path[i] = (double)n * h;
+}
+
+// ----------------------------------------------------------- launchers
+static int blocks_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
+                        const ScanLaunch& L, int num_sms, cudaStream_t st) {
+    cudaError_t err;
+    const int ne = L.n_events;
+    // stage the event hits into per-event drift tables
+    fill_kernel<<<num_sms * 4, 256, 0, st>>>(W.drift_tab, (long long)ne * G.n_wires, NOT_FIRED);
+    stage_kernel<<<num_sms * 4, 256, 0, st>>>(ne, L.hit_off, L.wire_id, L.drift, G.n_wires, P.max_drift,
+                                               W.drift_tab, L.flags);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    int occ = 0;
+    if (F.kind == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scan_kernel<0>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scan_kernel<1>, 256, 0);
+    const int scan_blocks = num_sms * (occ > 0 ? occ : 1);
+    for (int r = 0; r < L.n_rounds; ++r) {
+        const cdc_grid* grids = r == 0 ? L.grids0 : W.zgrids + (size_t)(r & 1) * W.max_events * CDC_MAX_ZOOM;
+        const int gpe = r == 0 ? 1 : CDC_MAX_ZOOM;
+        if (r > 0) {
+            const cdc_grid* pg = r == 1 ? L.grids0 : W.zgrids + (size_t)((r - 1) & 1) * W.max_events * CDC_MAX_ZOOM;
+            const int pgpe = r == 1 ? 1 : CDC_MAX_ZOOM;
+            const uint64_t* pk = W.round_keys + (size_t)((r - 1) & 1) * W.max_events * CDC_MAX_K;
+            cdc_grid* out = const_cast<cdc_grid*>(grids);
+            // slots beyond n_zoom stay empty grids
+            cudaMemsetAsync(out, 0, sizeof(cdc_grid) * (size_t)ne * CDC_MAX_ZOOM, st);
+            zoom_grid_kernel<<<blocks_for((long long)ne * L.n_zoom, 128), 128, 0, st>>>(
+                ne, L.n_zoom, r, pk, pg, pgpe, L.grids0, out,
+                L.zoom_grids ? L.zoom_grids + (size_t)r * ne * L.n_zoom : nullptr);
+        } else if (L.zoom_grids) {
+            record_round0_kernel<<<blocks_for((long long)ne * L.n_zoom, 128), 128, 0, st>>>(ne, L.n_zoom, L.grids0,
+                                                                                           L.zoom_grids);
+        }
+        float* E = (r == 0 && L.E0) ? L.E0 : W.E;
+        const long long cap = (r == 0 && L.E0) ? (1ll << 62) : W.e_cap;
+        prologue_kernel<<<1, 1024, 0, st>>>(ne, grids, gpe, cap, W.seg_cap, W.seed_off, W.seg_off, W.counters,
+                                            L.flags);
+        ScanIO io{W.drift_tab, L.hit_off, grids, gpe, W.seed_off, ne, W.counters, E, L.flags, L.steps};
+        if (F.kind == 0)
+            scan_kernel<0><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
+        else
+            scan_kernel<1><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
+        topk_partial_kernel<<<num_sms * 2, 256, 0, st>>>(E, W.seed_off, W.seg_off, ne, W.counters, P.k, W.seg_keys);
+        uint64_t* rk = W.round_keys + (size_t)(r & 1) * W.max_events * CDC_MAX_K;
+        topk_merge_kernel<<<blocks_for((long long)ne * 32, 256), 256, 0, st>>>(W.seg_off, ne, P.k, W.seg_keys, rk);
+        merge_best_kernel<<<blocks_for(ne, 64), 64, 0, st>>>(ne, P.k, r, rk, grids, gpe, W.best_keys, L.best_E,
+                                                             L.best_seed, L.topk0);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (L.hit_part || L.hit_res2) {
+        if (F.kind == 0)
+            assign_kernel<0><<<blocks_for(ne, 128), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
+                                                                  L.best_seed, P.k, L.hit_part, L.hit_res2);
+        else
+            assign_kernel<1><<<blocks_for(ne, 128), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
+                                                                  L.best_seed, P.k, L.hit_part, L.hit_res2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
+                             const float* seeds, int every, int n_rec, int precision, double* pos, int32_t* n_steps,
+                             double* path, cudaStream_t st) {
+    const int bs = 128, nb = blocks_for(n_seeds, bs);
+    if (precision == 0) {
+        if (F.kind == 0)
+            propagate_kernel<0><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+        else
+            propagate_kernel<1><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+    } else {
+        if (F.kind == 0)
+            propagate_fp64_kernel<0><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+        else
+            propagate_fp64_kernel<1><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cdc
