@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 seed-scanning track finder.
+
+Workload (one step = one event, the single-event multi-turn configuration):
+a 104.97 MeV/c e- making 2-3 turns in a finite-solenoid field map (451 x 1001
+samples at 2 mm), 10 % wire occupancy of DIO-like noise (e- uniform in 40-100
+MeV/c); circle Hough (512 x 512 int32) -> a 10^6-seed grid around the top
+peak (10 theta0 x 40 z0 x 10 px0 x 10 py0 x 25 pz0) -> ten scan rounds (the
+coarse grid plus nine zoom rounds of 4 x 3^5 seeds at halved steps) with up to
+3500 RKN steps of 2 mm and 3 turn partitions -> hit classification of the best
+seed.  Inputs are seeded synthetic events generated on the host.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "seeds/s and RKN steps/s at 1 GB300 (frac. of FP32 peak) vs FP64 CPU oracle; refine seeds/s"
+WORKLOAD = ("single multi-turn 104.97 MeV e- event, solenoid map 451x1001 @ 2 mm, 10% DIO-like occupancy; "
+            "circle Hough 512x512 -> 10^6-seed grid (10 theta0 x 40 z0 x 10 px0 x 10 py0 x 25 pz0); "
+            "10 scan rounds (coarse + 9 zoom x 4 x 3^5); RKN h=2 mm, <=3500 steps, 3 partitions; "
+            "hit classification of the best seed")
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
+H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
+
+
+def flops_per_step(kind: int) -> int:
+    """Algorithmic FP32 operations of one classical RKN step (FMA = 2):
+    field evaluation (map, x3): rho^2 3, sqrt 1, 1/rho 1, cell coordinates 4,
+    bilinear Bz and Br 6 + 6, Br/rho 1, Bx, By 2 = 24; k = lam t x B (x4): 12;
+    stage points t2, rm, t3, t4, re: 42; position update 21, direction update
+    15.  The compensation of the FP32 state (Kahan, 24) and the wire lookup
+    are not counted."""
+    field = 24 if kind == 1 else 0
+    return 3 * field + 4 * 12 + 42 + 21 + 15
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_workload(rank: int):
+    import cdc_synth as S
+    g = S.make_geometry()
+    fm = S.solenoid_map()
+    _, _, ev = S.cfg2_case(rank, fm, occupancy=0.10)
+    return g, fm, ev
+
+
+# --------------------------------------------------------------- CUDA arm
+def run_cuda(args, ws, rank, local):
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    from paper_1908_01949_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    g, fm, ev = make_workload(rank)
+    tmpl = S.cfg2_grid_template()
+    seeds_coarse = int(np.prod(tmpl["n"][0]))
+    seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
+    tr = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
+    hp = cdc.hough_params(grid_template=tmpl)
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
+                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    stream = torch.cuda.current_stream()
+    off_h = torch.tensor([0, ev.wire_id.size], dtype=torch.int32).pin_memory()
+    wid_h = torch.from_numpy(ev.wire_id.astype(np.int32)).pin_memory()
+    dr_h = torch.from_numpy(ev.drift.astype(np.float32)).pin_memory()
+    off, wid, dr = off_h.to(dev), wid_h.to(dev), dr_h.to(dev)
+    nh = wid.numel()
+    ne = 1
+    acc = torch.empty((ne, hp.n_bins, hp.n_bins), dtype=torch.int32, device=dev)
+    cand = torch.empty((ne, hp.max_cand, 28), dtype=torch.uint8, device=dev)
+    ncand = torch.empty(ne, dtype=torch.int32, device=dev)
+    grid = torch.empty((ne, cdc.GRID_BYTES), dtype=torch.uint8, device=dev)
+    hflags = torch.empty(ne, dtype=torch.int32, device=dev)
+    best_E = torch.empty((ne, K), dtype=torch.float32, device=dev)
+    best_seed = torch.empty((ne, K, 5), dtype=torch.float32, device=dev)
+    topk0 = torch.empty((ne, K), dtype=torch.int64, device=dev)
+    hit_part = torch.empty(nh, dtype=torch.int8, device=dev)
+    sflags = torch.empty(ne, dtype=torch.int32, device=dev)
+    steps = torch.zeros(N_ROUNDS, dtype=torch.int64, device=dev)
+    ctx = tr.ctx
+
+    def step(o, w, d):
+        ctx.cdc_hough_seeds(ne, o, w, hp, acc, cand, ncand, grid, hflags, stream)
+        ctx.cdc_scan_seeds(ne, o, w, d, grid, sp, None, topk0, best_E, best_seed, hit_part, None, None, sflags,
+                           steps, stream)
+
+    launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan fill+stage, 5/round, 9 zoom grids, assign
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    for _ in range(args.warmup):
+        step(off, wid, dr)
+    torch.cuda.synchronize()
+    steps.zero_()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.cdc_kernel_timer(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev_s[i].record(stream)
+        step(off, wid, dr)
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
+    ktot, kn, kper = ctx.cdc_kernel_time()
+    ctx.cdc_kernel_timer(False)
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rkn = steps.cpu().numpy().astype(np.float64)
+    rkn_per_step = float(rkn.sum()) / args.steps
+    coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
+    coarse_steps = float(rkn[0]) / args.steps
+    # roofline of the dominant kernel (coarse-round scan launch), ALU bound
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    f_step = flops_per_step(1)
+    achieved = f_step * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12 if coarse_ms else None
+
+    # end to end: host inputs -> device, the step, results -> host (pinned)
+    out_E = torch.empty((ne, K), dtype=torch.float32).pin_memory()
+    out_S = torch.empty((ne, K, 5), dtype=torch.float32).pin_memory()
+    out_P = torch.empty(nh, dtype=torch.int8).pin_memory()
+    out_F = torch.empty(ne, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    off2, wid2, dr2 = torch.empty_like(off), torch.empty_like(wid), torch.empty_like(dr)
+    for i in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        off2.copy_(off_h, non_blocking=True)
+        wid2.copy_(wid_h, non_blocking=True)
+        dr2.copy_(dr_h, non_blocking=True)
+        step(off2, wid2, dr2)
+        out_E.copy_(best_E, non_blocking=True)
+        out_S.copy_(best_seed, non_blocking=True)
+        out_P.copy_(hit_part, non_blocking=True)
+        out_F.copy_(sflags, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e = statistics.median(e2e_ms)
+    h2d = int(off_h.numel() * 4 + wid_h.numel() * 4 + dr_h.numel() * 4)
+    d2h = int(out_E.numel() * 4 + out_S.numel() * 4 + out_P.numel() + out_F.numel() * 4)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": ws * seeds_per_step / (ms / 1e3), "unit": "seeds/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "seeds_per_step": seeds_per_step, "events_per_step": 1,
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"event-parallel x{ws} (independent events per GPU, no collective)"},
+        "rkn_steps_per_s": ws * rkn_per_step / (ms / 1e3),
+        "coarse_scan": {"launch_ms": statistics.mean(coarse_ms) if coarse_ms else None, "rkn_steps": coarse_steps,
+                        "seeds": seeds_coarse},
+        "refine_seeds_per_s": None,
+        "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None, "flops_per_rkn_step": f_step,
+                     "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                   f"{sm_max:.0f} MHz (unit counts and max clock)"},
+        "e2e": {"value": seeds_per_step / (e2e / 1e3), "unit": "seeds/s", "ms_per_step": e2e,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "wall_s": wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(ev, g, fm, grid_t, target_s=15.0):
+    """FP64 oracle on a bounded random sample of this step's coarse seeds,
+    all host cores (threads split the seeds)."""
+    import oracle as O
+    import paper_1908_01949_gb300 as cdc
+    grid = cdc.tensor_to_grids(grid_t)
+    seeds = O.grid_values(grid[0:1])
+    rng = np.random.default_rng(0)
+    P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
+    cores = os.cpu_count() or 1
+    n = cores
+    t = 0.0
+    done = 0
+    steps = 0
+    while t < target_s and done < seeds.shape[0]:
+        idx = rng.choice(seeds.shape[0], size=min(n, seeds.shape[0]), replace=False)
+        t0 = time.perf_counter()
+        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=cores)
+        t += time.perf_counter() - t0
+        done += idx.size
+        steps += int(r["n_steps"].sum())
+        n *= 2
+    return {"value": done / t, "unit": "seeds/s", "cores": cores, "kind": "oracle",
+            "rkn_steps_per_s": steps / t,
+            "sample": f"{done} seeds drawn at random from the step's 10^6-seed coarse grid, same event and "
+                      f"parameters, {t:.1f} s"}
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args, ws, rank, local):
+    if rank != 0:
+        return
+    import cdc_synth as S
+    import oracle as O
+    oracle_build = O.build()
+    g, fm, ev = make_workload(0)
+    H_ = O.hough_params()
+    _, cand, cen = O.hough(g, H_, ev.wire_id)
+    tmpl = S.cfg2_grid_template()
+    if cen.shape[0]:
+        tmpl["centre"][0][[0, 2, 3]] = cen[0]
+    seeds = O.grid_values(tmpl)
+    P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    per_step = max(cores, int(args.ref_seeds))
+    times, done, nsteps = [], 0, 0
+    for i in range(args.warmup + args.steps):
+        idx = rng.choice(seeds.shape[0], size=per_step, replace=False)
+        t0 = time.perf_counter()
+        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            done += per_step
+            nsteps += int(r["n_steps"].sum())
+    tot = sum(times)
+    v = done / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "seeds/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "seeds_per_step": per_step,
+                       "sample": f"{per_step} seeds per step drawn from the 10^6-seed grid of the same event"},
+            "rkn_steps_per_s": nsteps / tot,
+            "cpu_baseline": {"value": v, "unit": "seeds/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random seeds of the coarse grid per step ({oracle_build})"},
+            "e2e": {"value": v, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seeds", type=int, default=512, help="oracle seeds per step of the reference arm")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+    else:
+        run_cuda(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

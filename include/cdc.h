@@ -192,8 +192,8 @@ int cdc_hough_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const in
  * best_seed [n_events][k][5] (best over all rounds), hit_part [hits]
  * (nullable), hit_res2 [hits] (nullable; best squared residual of the best
  * seed), zoom_grids [n_rounds][n_events][n_zoom] (nullable; the grids of each
- * round, round 0 in slot 0), flags [n_events], steps (nullable, 1 counter:
- * RKN steps executed, accumulated).
+ * round, round 0 in slot 0), flags [n_events], steps (nullable, [n_rounds]
+ * counters: RKN steps executed in each round, added to the current values).
  * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
 int cdc_scan_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id,
                    const float* drift, const cdc_grid* grids, const cdc_scan_params* params, float* E,
@@ -206,15 +206,17 @@ int cdc_scan_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int
  * then n_iter iterations minimise chi^2 = sum over classified hits of
  * ((DCA_k - drift)/sigma)^2 with J from forward tangents of the RKN step and
  * an FP64 Cholesky solve of the 5x5 normal equations in units of scale.
- * Device inputs: seed_event [n_seeds] (event of each seed), seeds
- * [n_seeds][5], hit_off, wire_id, drift.  Device outputs: seeds_out
+ * Device inputs: seed_event [n_seeds] (event of each seed, in [0, n_events);
+ * a seed with another value gets CDC_FLAG_BAD_HIT and NaN outputs), seeds
+ * [n_seeds][5], hit_off [n_events+1], wire_id, drift.  Device outputs: seeds_out
  * [n_seeds][5], chi2 [n_seeds] (FP64, at the refined seed), grad [n_seeds][5]
  * (nullable; d chi^2 / d seed at the refined seed from the adjoint RKN with
  * checkpoints every `checkpoint` steps), n_used [n_seeds] (nullable), flags
  * [n_seeds].  scan supplies h, max_steps, lambda, max_partitions, direction,
- * charge, max_drift.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED,
- * CDC_ERR_CUDA. */
-int cdc_refine_seeds(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds,
+ * charge, max_drift; max_steps must stay below 64 * checkpoint.  Uses the
+ * context's drift-table workspace (n_events <= reserved events).
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
+int cdc_refine_seeds(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds, int n_events,
                      const int32_t* hit_off, const int32_t* wire_id, const float* drift,
                      const cdc_scan_params* scan, const cdc_refine_params* params, float* seeds_out,
                      double* chi2, float* grad, int32_t* n_used, uint32_t* flags, void* stream);
@@ -223,7 +225,7 @@ int cdc_refine_seeds(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const
  * backward half of cdc_refine_seeds, exposed for autograd).  Hit
  * classification as in cdc_refine_seeds, at the given seed.  Device outputs:
  * chi2 [n_seeds] (FP64), grad [n_seeds][5] (nullable).  Errors as above. */
-int cdc_chi2_grad(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds,
+int cdc_chi2_grad(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const float* seeds, int n_events,
                   const int32_t* hit_off, const int32_t* wire_id, const float* drift,
                   const cdc_scan_params* scan, const cdc_refine_params* params, double* chi2, float* grad,
                   int32_t* n_used, uint32_t* flags, void* stream);
@@ -232,11 +234,23 @@ int cdc_chi2_grad(cdc_ctx* ctx, int n_seeds, const int32_t* seed_event, const fl
  * positions and for the precision sweep).  Each seed is propagated with the
  * scan's stop rules; every `every` steps (starting at step `every`) the
  * position is written, up to n_rec records.  precision 0: FP32 with
- * compensated state (the scan's stepper); 1: FP64.  Device outputs: pos
+ * compensated state (the scan's stepper); 1: FP64; 2: FP32 with compensated
+ * state and a two-float q/p (the refine's stepper).  Device outputs: pos
  * [n_seeds][n_rec][3] float64 (NaN after the track ended), n_steps [n_seeds],
  * path [n_seeds] (FP64 path length).  Errors as above. */
 int cdc_propagate(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_params* scan, int every,
                   int n_rec, int precision, double* pos, int32_t* n_steps, double* path, void* stream);
+
+/* Kernel timer for measurement (no counterpart in the paper): while enabled,
+ * CUDA events are recorded on the call's stream immediately before and after
+ * every launch of the seed-scan kernel (the scan's dominant kernel), up to
+ * 1024 launches.  cdc_kernel_time waits for the recorded events, returns the
+ * summed device time [ms], the number of timed launches since the last read
+ * and (per_launch_ms nullable, host, cap entries) each launch's time in launch
+ * order, and clears them.  Do not enable it while capturing a CUDA graph.
+ * Errors: CDC_ERR_ARG, CDC_ERR_CUDA. */
+int cdc_kernel_timer(cdc_ctx* ctx, int enable);
+int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* per_launch_ms, int cap);
 
 #ifdef __cplusplus
 }

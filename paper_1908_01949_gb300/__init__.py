@@ -69,7 +69,7 @@ class Tracker:
         out = dict(best_E=t.empty((ne, K), dtype=t.float32, device=self.dev),
                    best_seed=t.empty((ne, K, 5), dtype=t.float32, device=self.dev),
                    flags=t.empty(ne, dtype=t.int32, device=self.dev),
-                   steps=t.zeros(1, dtype=t.int64, device=self.dev))
+                   steps=t.zeros(params.n_rounds, dtype=t.int64, device=self.dev))
         out["E"] = t.empty(int(n_seeds), dtype=t.float32, device=self.dev) if want_E else None
         out["topk0"] = t.empty((ne, K), dtype=t.int64, device=self.dev) if want_topk0 else None
         nh = int(wire_id.numel())
@@ -101,8 +101,8 @@ class Tracker:
                    grad=t.empty((n, 5), dtype=t.float32, device=self.dev) if want_grad else None,
                    n_used=t.empty(n, dtype=t.int32, device=self.dev),
                    flags=t.empty(n, dtype=t.int32, device=self.dev))
-        self.ctx.cdc_refine_seeds(n, seed_event, seeds, hit_off, wire_id, drift, scan, params, out["seeds"],
-                                  out["chi2"], out["grad"], out["n_used"], out["flags"], stream)
+        self.ctx.cdc_refine_seeds(n, seed_event, seeds, int(hit_off.numel()) - 1, hit_off, wire_id, drift, scan,
+                                  params, out["seeds"], out["chi2"], out["grad"], out["n_used"], out["flags"], stream)
         return out
 
     def chi2_grad(self, seed_event, seeds, hit_off, wire_id, drift, scan, params, want_grad=True, stream=None):
@@ -112,8 +112,8 @@ class Tracker:
                    grad=t.empty((n, 5), dtype=t.float32, device=self.dev) if want_grad else None,
                    n_used=t.empty(n, dtype=t.int32, device=self.dev),
                    flags=t.empty(n, dtype=t.int32, device=self.dev))
-        self.ctx.cdc_chi2_grad(n, seed_event, seeds, hit_off, wire_id, drift, scan, params, out["chi2"], out["grad"],
-                               out["n_used"], out["flags"], stream)
+        self.ctx.cdc_chi2_grad(n, seed_event, seeds, int(hit_off.numel()) - 1, hit_off, wire_id, drift, scan, params,
+                               out["chi2"], out["grad"], out["n_used"], out["flags"], stream)
         return out
 
 

@@ -33,7 +33,8 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 
 # All entry points of include/cdc.h.
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
-           "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate"]
+           "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
+           "cdc_kernel_timer", "cdc_kernel_time"]
 
 
 class cdc_grid(C.Structure):
@@ -94,11 +95,13 @@ def lib():
         L.cdc_hough_seeds.argtypes = [vp, C.c_int, vp, vp, P(cdc_hough_params), vp, vp, vp, vp, vp, vp]
         L.cdc_scan_seeds.argtypes = [vp, C.c_int, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp, vp]
-        L.cdc_refine_seeds.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, P(cdc_scan_params), P(cdc_refine_params), vp,
-                                       vp, vp, vp, vp, vp]
-        L.cdc_chi2_grad.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, P(cdc_scan_params), P(cdc_refine_params), vp, vp,
-                                    vp, vp, vp]
+        L.cdc_refine_seeds.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp, vp, vp, P(cdc_scan_params),
+                                       P(cdc_refine_params), vp, vp, vp, vp, vp, vp]
+        L.cdc_chi2_grad.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp, vp, vp, P(cdc_scan_params), P(cdc_refine_params),
+                                    vp, vp, vp, vp, vp]
         L.cdc_propagate.argtypes = [vp, C.c_int, vp, P(cdc_scan_params), C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+        L.cdc_kernel_timer.argtypes = [vp, C.c_int]
+        L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
         for name in EXPORTS:
             if name not in ("cdc_destroy", "cdc_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -252,28 +255,38 @@ class Context:
             _dev(zoom_grids, torch.uint8, "zoom_grids", d, True), _dev(flags, torch.int32, "flags", d),
             _dev(steps, torch.int64, "steps", d, True), _stream(stream)))
 
-    def cdc_refine_seeds(self, n_seeds, seed_event, seeds, hit_off, wire_id, drift, scan, params, seeds_out, chi2,
-                         grad, n_used, flags, stream=None):
+    def cdc_refine_seeds(self, n_seeds, seed_event, seeds, n_events, hit_off, wire_id, drift, scan, params,
+                         seeds_out, chi2, grad, n_used, flags, stream=None):
         import torch
         d = self.device
         return self._check(self.L.cdc_refine_seeds(
             self.h, int(n_seeds), _dev(seed_event, torch.int32, "seed_event", d), _dev(seeds, torch.float32, "seeds", d),
-            _dev(hit_off, torch.int32, "hit_off", d), _dev(wire_id, torch.int32, "wire_id", d),
+            int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(wire_id, torch.int32, "wire_id", d),
             _dev(drift, torch.float32, "drift", d), C.byref(scan), C.byref(params),
             _dev(seeds_out, torch.float32, "seeds_out", d), _dev(chi2, torch.float64, "chi2", d),
             _dev(grad, torch.float32, "grad", d, True), _dev(n_used, torch.int32, "n_used", d, True),
             _dev(flags, torch.int32, "flags", d), _stream(stream)))
 
-    def cdc_chi2_grad(self, n_seeds, seed_event, seeds, hit_off, wire_id, drift, scan, params, chi2, grad, n_used,
-                      flags, stream=None):
+    def cdc_chi2_grad(self, n_seeds, seed_event, seeds, n_events, hit_off, wire_id, drift, scan, params, chi2, grad,
+                      n_used, flags, stream=None):
         import torch
         d = self.device
         return self._check(self.L.cdc_chi2_grad(
             self.h, int(n_seeds), _dev(seed_event, torch.int32, "seed_event", d), _dev(seeds, torch.float32, "seeds", d),
-            _dev(hit_off, torch.int32, "hit_off", d), _dev(wire_id, torch.int32, "wire_id", d),
+            int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(wire_id, torch.int32, "wire_id", d),
             _dev(drift, torch.float32, "drift", d), C.byref(scan), C.byref(params),
             _dev(chi2, torch.float64, "chi2", d), _dev(grad, torch.float32, "grad", d, True),
             _dev(n_used, torch.int32, "n_used", d, True), _dev(flags, torch.int32, "flags", d), _stream(stream)))
+
+    def cdc_kernel_timer(self, enable):
+        return self._check(self.L.cdc_kernel_timer(self.h, int(bool(enable))))
+
+    def cdc_kernel_time(self, cap=2048):
+        """(summed device ms, launches, per-launch ms) of the timed scan-kernel launches."""
+        ms, n = C.c_double(0), C.c_int64(0)
+        per = np.zeros(cap, np.float32)
+        self._check(self.L.cdc_kernel_time(self.h, C.byref(ms), C.byref(n), per.ctypes.data, int(cap)))
+        return ms.value, n.value, per[:min(n.value, cap)].copy()
 
     def cdc_propagate(self, n_seeds, seeds, params, every, n_rec, precision, pos, n_steps, path, stream=None):
         import torch

@@ -27,6 +27,7 @@ struct cdc_ctx {
     float4* d_wires = nullptr;
     uchar2* d_tab = nullptr;
     int2* d_wire_um = nullptr;
+    float4* d_wires_lo = nullptr;
     double tan_max = 0.0;
     // field
     bool field = false;
@@ -38,6 +39,10 @@ struct cdc_ctx {
     int2* d_offsets = nullptr;
     size_t offsets_cap = 0;
     int off_key[4] = {-1, -1, -1, -1};
+    // kernel timer
+    bool timer_on = false;
+    std::vector<cudaEvent_t> timer_ev;
+    int timer_used = 0;
 };
 
 namespace {
@@ -113,14 +118,15 @@ int check_scan_params(cdc_ctx* c, const cdc_scan_params* p, bool need_k) {
         if (p->n_rounds > 1 && (p->n_zoom < 1 || p->n_zoom > CDC_MAX_ZOOM || p->n_zoom > p->k))
             return fail(c, CDC_ERR_RANGE, "n_zoom outside 1..min(k, 8)");
     }
-    if (search_width(c, p) > TAB_BAND)
-        return fail(c, CDC_ERR_RANGE, "max_drift + sqrt(lambda) too large for the wire search window");
+    if (search_width(c, p) + 4.0f * p->h > TAB_BAND)  // the candidate lists widen the window by 4 h
+        return fail(c, CDC_ERR_RANGE, "max_drift + sqrt(lambda) (or h) too large for the wire search window");
     return CDC_OK;
 }
 
 ScanConst make_const(const cdc_ctx* c, const cdc_scan_params* p) {
     ScanConst P{};
     P.h = p->h;
+    P.h6_lo = (float)((double)p->h / 6.0 - (double)(p->h * (1.0f / 6.0f)));
     P.lam = p->lambda;
     P.charge_dir = p->charge * (float)p->direction;
     P.band = search_width(c, p);
@@ -161,9 +167,11 @@ void cdc_destroy(cdc_ctx* c) {
     dfree(c->d_wires);
     dfree(c->d_tab);
     dfree(c->d_wire_um);
+    dfree(c->d_wires_lo);
     dfree(c->d_cells);
     dfree(c->d_offsets);
     free_workspace(c->W);
+    for (cudaEvent_t e : c->timer_ev) cudaEventDestroy(e);
     delete c;
 }
 
@@ -193,6 +201,7 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
     std::vector<DevLayer> lay(n_layers);
     std::vector<float4> wires(nw);
     std::vector<int2> wum(nw);
+    std::vector<float4> wlo(nw);
     int base = 0;
     for (int l = 0; l < n_layers; ++l) {
         DevLayer& L = lay[l];
@@ -204,6 +213,7 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
         L.n_over_2pi = (float)(N[l] / (2.0 * PI));
         L.cells_per_mm = (float)(N[l] / (2.0 * PI * (R[l] - TAB_BAND)) * 1.01);
         L.cosa = (float)cos(alpha[l]);
+        L.cosa_lo = (float)(cos(alpha[l]) - (double)L.cosa);
         L.N = N[l];
         L.base = base;
         double sa = sin(alpha[l]);
@@ -212,6 +222,9 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
             double mx = R[l] * cos(phi), my = R[l] * sin(phi);
             wires[base + i] = make_float4((float)mx, (float)my, (float)(-sa * sin(phi)), (float)(sa * cos(phi)));
             wum[base + i] = make_int2((int)llround(1000.0 * mx), (int)llround(1000.0 * my));
+            const double dx = -sa * sin(phi), dy = sa * cos(phi);
+            wlo[base + i] = make_float4((float)(mx - (double)(float)mx), (float)(my - (double)(float)my),
+                                        (float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
         }
         base += N[l];
     }
@@ -232,17 +245,20 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
     DeviceGuard g(c->device);
     cudaError_t e;
     if ((e = dalloc(c->d_layers, lay.size())) != cudaSuccess || (e = dalloc(c->d_wires, wires.size())) != cudaSuccess ||
-        (e = dalloc(c->d_tab, tab.size())) != cudaSuccess || (e = dalloc(c->d_wire_um, wum.size())) != cudaSuccess)
+        (e = dalloc(c->d_tab, tab.size())) != cudaSuccess || (e = dalloc(c->d_wire_um, wum.size())) != cudaSuccess ||
+        (e = dalloc(c->d_wires_lo, wlo.size())) != cudaSuccess)
         return fail(c, CDC_ERR_NOMEM, std::string("geometry allocation: ") + cudaGetErrorString(e));
     if ((e = cudaMemcpy(c->d_layers, lay.data(), lay.size() * sizeof(DevLayer), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c->d_wires, wires.data(), wires.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c->d_tab, tab.data(), tab.size() * sizeof(uchar2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c->d_wire_um, wum.data(), wum.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaMemcpy(c->d_wire_um, wum.data(), wum.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_wires_lo, wlo.data(), wlo.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(c, e, "geometry upload");
     c->G.layers = c->d_layers;
     c->G.wires = c->d_wires;
     c->G.tab = c->d_tab;
     c->G.wire_um = c->d_wire_um;
+    c->G.wires_lo = c->d_wires_lo;
     c->G.n_layers = n_layers;
     c->G.n_wires = nw;
     c->G.z_half = (float)z_half;
@@ -400,30 +416,65 @@ int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32
     cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_events, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "flags reset");
     ScanLaunch L{n_events, hit_off, wire_id, drift, grids, E, topk0, best_E, best_seed, hit_part, hit_res2, zoom_grids,
-                 flags, steps, p->n_rounds, p->n_rounds > 1 ? p->n_zoom : 1};
+                 flags, steps, p->n_rounds, p->n_rounds > 1 ? p->n_zoom : 1, KernelTimer{}};
+    if (c->timer_on) L.timer = KernelTimer{c->timer_ev.data(), (int)c->timer_ev.size(), &c->timer_used};
     e = launch_scan(c->G, c->F, make_const(c, p), c->W, L, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scan launch");
     return CDC_OK;
 }
 
-int cdc_refine_seeds(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, const int32_t* hit_off,
-                     const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
+}  // extern "C"
+
+namespace {
+int refine_common(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, int n_events,
+                  const int32_t* hit_off, const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
+                  const cdc_refine_params* rp, float* seeds_out, double* chi2, float* grad, int32_t* n_used,
+                  uint32_t* flags, void* stream, int do_gn) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (n_seeds < 0 || n_events < 0) return fail(c, CDC_ERR_ARG, "n_seeds, n_events < 0");
+    if (n_seeds == 0) return CDC_OK;
+    int rc = check_scan_params(c, scan, false);
+    if (rc) return rc;
+    if (!rp) return fail(c, CDC_ERR_ARG, "refine params is NULL");
+    if (!seed_event || !seeds || !hit_off || !wire_id || !drift || !chi2 || !flags || (do_gn && !seeds_out))
+        return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (n_events < 1) return fail(c, CDC_ERR_ARG, "n_events must be >= 1");
+    if (rp->n_iter < 0 || rp->n_iter > 32) return fail(c, CDC_ERR_RANGE, "n_iter outside 0..32");
+    if (!(rp->sigma > 0.f)) return fail(c, CDC_ERR_ARG, "sigma must be > 0");
+    for (int m = 0; m < 5; ++m)
+        if (!(rp->scale[m] > 0.f)) return fail(c, CDC_ERR_ARG, "scales must be > 0");
+    if (rp->checkpoint < 8 || rp->checkpoint > 256) return fail(c, CDC_ERR_RANGE, "checkpoint outside 8..256");
+    if (scan->max_steps >= 64 * rp->checkpoint) return fail(c, CDC_ERR_RANGE, "max_steps >= 64 * checkpoint");
+    if (n_events > c->W.max_events || c->W.n_wires < c->G.n_wires)
+        return fail(c, CDC_ERR_NOT_LOADED, "workspace too small: call cdc_reserve");
+    DeviceGuard g(c->device);
+    RefineLaunch L{n_seeds, seed_event, seeds, n_events, hit_off, wire_id, drift, rp->n_iter, rp->sigma,
+                   {rp->scale[0], rp->scale[1], rp->scale[2], rp->scale[3], rp->scale[4]}, rp->checkpoint, seeds_out,
+                   chi2, grad, n_used, flags};
+    cudaError_t e = launch_refine(c->G, c->F, make_const(c, scan), L, c->W.drift_tab, c->num_sms, do_gn,
+                                  (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "refine launch");
+    return CDC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int cdc_refine_seeds(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, int n_events,
+                     const int32_t* hit_off, const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
                      const cdc_refine_params* params, float* seeds_out, double* chi2, float* grad, int32_t* n_used,
                      uint32_t* flags, void* stream) {
-    if (!c) return CDC_ERR_ARG;
-    (void)n_seeds; (void)seed_event; (void)seeds; (void)hit_off; (void)wire_id; (void)drift; (void)scan;
-    (void)params; (void)seeds_out; (void)chi2; (void)grad; (void)n_used; (void)flags; (void)stream;
-    return fail(c, CDC_ERR_RANGE, "refine: not built yet");
+    return refine_common(c, n_seeds, seed_event, seeds, n_events, hit_off, wire_id, drift, scan, params, seeds_out,
+                         chi2, grad, n_used, flags, stream, 1);
 }
 
-int cdc_chi2_grad(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, const int32_t* hit_off,
-                  const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
+int cdc_chi2_grad(cdc_ctx* c, int n_seeds, const int32_t* seed_event, const float* seeds, int n_events,
+                  const int32_t* hit_off, const int32_t* wire_id, const float* drift, const cdc_scan_params* scan,
                   const cdc_refine_params* params, double* chi2, float* grad, int32_t* n_used, uint32_t* flags,
                   void* stream) {
-    if (!c) return CDC_ERR_ARG;
-    (void)n_seeds; (void)seed_event; (void)seeds; (void)hit_off; (void)wire_id; (void)drift; (void)scan;
-    (void)params; (void)chi2; (void)grad; (void)n_used; (void)flags; (void)stream;
-    return fail(c, CDC_ERR_RANGE, "chi2_grad: not built yet");
+    return refine_common(c, n_seeds, seed_event, seeds, n_events, hit_off, wire_id, drift, scan, params, nullptr,
+                         chi2, grad, n_used, flags, stream, 0);
 }
 
 int cdc_propagate(cdc_ctx* c, int n_seeds, const float* seeds, const cdc_scan_params* p, int every, int n_rec,
@@ -436,11 +487,43 @@ int cdc_propagate(cdc_ctx* c, int n_seeds, const float* seeds, const cdc_scan_pa
     if (rc) return rc;
     if (!seeds || !pos || !n_steps || !path) return fail(c, CDC_ERR_ARG, "NULL argument");
     if (every < 1 || n_rec < 1) return fail(c, CDC_ERR_ARG, "every and n_rec must be >= 1");
-    if (precision != 0 && precision != 1) return fail(c, CDC_ERR_ARG, "precision must be 0 or 1");
+    if (precision < 0 || precision > 2) return fail(c, CDC_ERR_ARG, "precision must be 0, 1 or 2");
     DeviceGuard g(c->device);
     cudaError_t e = launch_propagate(c->G, c->F, make_const(c, p), n_seeds, seeds, every, n_rec, precision, pos,
                                      n_steps, path, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
+    return CDC_OK;
+}
+
+int cdc_kernel_timer(cdc_ctx* c, int enable) {
+    if (!c) return CDC_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (enable && c->timer_ev.empty()) {
+        c->timer_ev.resize(2048);
+        for (auto& e : c->timer_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CDC_ERR_CUDA, "cudaEventCreate");
+    }
+    c->timer_on = enable != 0;
+    c->timer_used = 0;
+    return CDC_OK;
+}
+
+int cdc_kernel_time(cdc_ctx* c, double* total_ms, int64_t* launches, float* per_launch_ms, int cap) {
+    if (!c || !total_ms || !launches) return c ? fail(c, CDC_ERR_ARG, "NULL argument") : CDC_ERR_ARG;
+    DeviceGuard g(c->device);
+    double tot = 0.0;
+    for (int i = 0; i + 1 < c->timer_used; i += 2) {
+        cudaError_t e = cudaEventSynchronize(c->timer_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel timer");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->timer_ev[i], c->timer_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel timer");
+        tot += ms;
+        if (per_launch_ms && i / 2 < cap) per_launch_ms[i / 2] = ms;
+    }
+    *total_ms = tot;
+    *launches = c->timer_used / 2;
+    c->timer_used = 0;
     return CDC_OK;
 }
 

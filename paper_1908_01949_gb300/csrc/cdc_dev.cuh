@@ -27,7 +27,7 @@ struct DevLayer {
     float n_over_2pi;    // N / (2 pi): cells per radian
     float cells_per_mm;  // N / (2 pi (R - TAB_BAND)): conservative cells per mm of arc
     float cosa;          // cos(alpha): z component of the wire direction
-    float pad;
+    float cosa_lo;       // cos(alpha) - cosa, the rounding residual
     int N;               // wires in the layer
     int base;            // global id of wire 0
     int pad2, pad3;
@@ -39,6 +39,7 @@ struct DevGeom {
     const float4* wires;     // [n_wires]: (mx, my, dx, dy) of the wire line (m at z = 0; dz = layer cosa)
     const uchar2* tab;       // [TAB_N]: (first, last) layer whose band may contain rho in [b, b+1) mm
     const int2* wire_um;     // [n_wires]: wire (x, y) at z = 0 rounded to um (Hough input)
+    const float4* wires_lo;  // [n_wires]: rounding residuals of (mx, my, dx, dy) in `wires`
     int n_layers, n_wires;
     float z_half, R0, R_out;
     double R0d;
@@ -56,7 +57,7 @@ struct DevField {
 
 // Scan-call parameters, resolved on the host.
 struct ScanConst {
-    float h, lam, charge_dir, band, d_win, max_drift;
+    float h, h6_lo, lam, charge_dir, band, d_win, max_drift;  // h6_lo = h/6 - float(h/6)
     int max_steps, max_part, direction, k;
 };
 
@@ -70,8 +71,8 @@ __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, 
         bz = F.B0;
     } else {
         float r2 = fmaf(x, x, y * y);
-        float rho = sqrtf(r2);
-        float rinv = rho > 0.f ? 1.0f / rho : 0.f;
+        float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        float rho = r2 * rinv;
         float rc = fminf(fmaxf(rho, F.r_min), F.r_max);
         float zc = fminf(fmaxf(z, F.z_min), F.z_max);
         float u = (rc - F.r_min) * F.inv_dr;
@@ -97,7 +98,7 @@ __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, 
 struct State {
     float rx, ry, rz, lx, ly, lz;  // position hi / lo
     float tx, ty, tz, mx, my, mz;  // direction hi / lo
-    float lam;
+    float lam, lam_lo;             // q kappa / p as hi + lo (lo used by the refine path only)
 };
 
 __device__ __forceinline__ void kahan(float& hi, float& lo, float inc) {
@@ -107,6 +108,17 @@ __device__ __forceinline__ void kahan(float& hi, float& lo, float inc) {
     hi = s;
 }
 
+// (hi, lo) += inc + inc_lo as a two-float sum: the error of hi + inc (Fast2Sum)
+// and inc_lo accumulate in the low word, which then renormalises.  Unlike the
+// Kahan form above, a low word far below an ulp of the increment is kept.
+__device__ __forceinline__ void acc2(float& hi, float& lo, float inc, float inc_lo) {
+    const float s = hi + inc;
+    const float e = inc - (s - hi);
+    const float l = lo + (e + inc_lo);
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
 __device__ __forceinline__ void cross_lam(float lam, float ax, float ay, float az, float bx, float by, float bz,
                                           float& cx, float& cy, float& cz) {
     cx = lam * fmaf(ay, bz, -az * by);
@@ -114,45 +126,89 @@ __device__ __forceinline__ void cross_lam(float lam, float ax, float ay, float a
     cz = lam * fmaf(ax, by, -ay * bx);
 }
 
+// (lam + lam_lo) (a x b): the curvature with a two-float lam, rounded once
+// (fma(lam, x, lam_lo x)); rounding lam x first would leave a bias of up to
+// half an ulp that acts like a scaled curvature at every step
+__device__ __forceinline__ void cross_lam2(float lam, float lo, float ax, float ay, float az, float bx, float by,
+                                           float bz, float& cx, float& cy, float& cz) {
+    const float x = fmaf(ay, bz, -az * by), y = fmaf(az, bx, -ax * bz), z = fmaf(ax, by, -ay * bx);
+    cx = fmaf(lam, x, lo * x);
+    cy = fmaf(lam, y, lo * y);
+    cz = fmaf(lam, z, lo * z);
+}
+
+// k = lam (a x b) with lam in one float (scan) or two (refine: PRECISE)
+template <bool PRECISE>
+__device__ __forceinline__ void kvec(const State& s, float ax, float ay, float az, float bx, float by, float bz,
+                                     float& cx, float& cy, float& cz) {
+    if (PRECISE)
+        cross_lam2(s.lam, s.lam_lo, ax, ay, az, bx, by, bz, cx, cy, cz);
+    else
+        cross_lam(s.lam, ax, ay, az, bx, by, bz, cx, cy, cz);
+}
+
 // One classical Runge-Kutta-Nystrom step of length h (Abramowitz & Stegun
 // 25.5.20) for r'' = lam (r' x B(r)): field at the start, at the midpoint
 // r + h/2 t + h^2/8 k1 (shared by k2 and k3) and at r + h t + h^2/2 k3.  The
-// increments are formed in FP32 and added to the compensated state.
-template <int KIND>
-__device__ __forceinline__ void rkn_step(const DevField& F, State& s, float h) {
+// increments are formed in FP32 and added to the compensated state
+// (PRECISE: two-float q/p and two-float sums, for the refine path).
+template <int KIND, bool PRECISE = false>
+__device__ __forceinline__ void rkn_step(const DevField& F, State& s, float h, float h6_lo) {
     const float h2 = 0.5f * h, hh8 = h * h * 0.125f, hh2 = h * h * 0.5f, hh6 = h * h * (1.0f / 6.0f),
                 h6 = h * (1.0f / 6.0f);
     float bx, by, bz;
     float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
     field_eval<KIND>(F, s.rx, s.ry, s.rz, bx, by, bz);
-    cross_lam(s.lam, s.tx, s.ty, s.tz, bx, by, bz, k1x, k1y, k1z);
+    kvec<PRECISE>(s, s.tx, s.ty, s.tz, bx, by, bz, k1x, k1y, k1z);
     float px = fmaf(hh8, k1x, fmaf(h2, s.tx, s.rx));
     float py = fmaf(hh8, k1y, fmaf(h2, s.ty, s.ry));
     float pz = fmaf(hh8, k1z, fmaf(h2, s.tz, s.rz));
     if (KIND != 0) field_eval<KIND>(F, px, py, pz, bx, by, bz);
-    cross_lam(s.lam, fmaf(h2, k1x, s.tx), fmaf(h2, k1y, s.ty), fmaf(h2, k1z, s.tz), bx, by, bz, k2x, k2y, k2z);
-    cross_lam(s.lam, fmaf(h2, k2x, s.tx), fmaf(h2, k2y, s.ty), fmaf(h2, k2z, s.tz), bx, by, bz, k3x, k3y, k3z);
+    kvec<PRECISE>(s, fmaf(h2, k1x, s.tx), fmaf(h2, k1y, s.ty), fmaf(h2, k1z, s.tz), bx, by, bz, k2x, k2y, k2z);
+    kvec<PRECISE>(s, fmaf(h2, k2x, s.tx), fmaf(h2, k2y, s.ty), fmaf(h2, k2z, s.tz), bx, by, bz, k3x, k3y, k3z);
     if (KIND != 0) {
         px = fmaf(hh2, k3x, fmaf(h, s.tx, s.rx));
         py = fmaf(hh2, k3y, fmaf(h, s.ty, s.ry));
         pz = fmaf(hh2, k3z, fmaf(h, s.tz, s.rz));
         field_eval<KIND>(F, px, py, pz, bx, by, bz);
     }
-    cross_lam(s.lam, fmaf(h, k3x, s.tx), fmaf(h, k3y, s.ty), fmaf(h, k3z, s.tz), bx, by, bz, k4x, k4y, k4z);
-    // position: h (t_hi + t_lo) + h^2/6 (k1 + k2 + k3)
-    float drx = fmaf(h, s.tx, fmaf(h, s.mx, hh6 * (k1x + k2x + k3x)));
-    float dry = fmaf(h, s.ty, fmaf(h, s.my, hh6 * (k1y + k2y + k3y)));
-    float drz = fmaf(h, s.tz, fmaf(h, s.mz, hh6 * (k1z + k2z + k3z)));
-    // direction: h/6 (k1 + 2 k2 + 2 k3 + k4)
-    float dtx = h6 * (k1x + k4x + 2.0f * (k2x + k3x));
-    float dty = h6 * (k1y + k4y + 2.0f * (k2y + k3y));
-    float dtz = h6 * (k1z + k4z + 2.0f * (k2z + k3z));
-    kahan(s.rx, s.lx, drx);
-    kahan(s.ry, s.ly, dry);
-    kahan(s.rz, s.lz, drz);
-    kahan(s.tx, s.mx, dtx);
-    kahan(s.ty, s.my, dty);
-    kahan(s.tz, s.mz, dtz);
+    kvec<PRECISE>(s, fmaf(h, k3x, s.tx), fmaf(h, k3y, s.ty), fmaf(h, k3z, s.tz), bx, by, bz, k4x, k4y, k4z);
+    // position: h (t_hi + t_lo) + h^2/6 (k1 + k2 + k3); h t_lo lies below half
+    // an ulp of the increment, so it goes straight into the low word (folding it
+    // into the rounded increment would drop it at every step)
+    float drx = fmaf(h, s.tx, hh6 * (k1x + k2x + k3x));
+    float dry = fmaf(h, s.ty, hh6 * (k1y + k2y + k3y));
+    float drz = fmaf(h, s.tz, hh6 * (k1z + k2z + k3z));
+    const float clx = h * s.mx, cly = h * s.my, clz = h * s.mz;
+    // direction: h/6 (k1 + 2 k2 + 2 k3 + k4) as a two-float increment: the
+    // rounding of the product and of the constant h/6 (which alone would scale
+    // the curvature by up to 3e-8 at every step) go to the low word
+    const float sx = k1x + k4x + 2.0f * (k2x + k3x), sy = k1y + k4y + 2.0f * (k2y + k3y),
+                sz = k1z + k4z + 2.0f * (k2z + k3z);
+    const float dtx = h6 * sx, dty = h6 * sy, dtz = h6 * sz;
+    const float dlx = fmaf(h6_lo, sx, fmaf(h6, sx, -dtx)), dly = fmaf(h6_lo, sy, fmaf(h6, sy, -dty)),
+                dlz = fmaf(h6_lo, sz, fmaf(h6, sz, -dtz));
+    if (PRECISE) {  // refine: two-float sums (gradients to 1e-4 need ~1e-6 mm)
+        acc2(s.rx, s.lx, drx, clx);
+        acc2(s.ry, s.ly, dry, cly);
+        acc2(s.rz, s.lz, drz, clz);
+        acc2(s.tx, s.mx, dtx, dlx);
+        acc2(s.ty, s.my, dty, dly);
+        acc2(s.tz, s.mz, dtz, dlz);
+    } else {        // scan: compensated sums, ~5e-5 mm per metre
+        kahan(s.rx, s.lx, drx);
+        kahan(s.ry, s.ly, dry);
+        kahan(s.rz, s.lz, drz);
+        s.lx += clx;
+        s.ly += cly;
+        s.lz += clz;
+        kahan(s.tx, s.mx, dtx);
+        kahan(s.ty, s.my, dty);
+        kahan(s.tz, s.mz, dtz);
+        s.mx += dlx;
+        s.my += dly;
+        s.mz += dlz;
+    }
 }
 
 // Seed (theta0, z0, px0, py0, pz0) at r = R0 -> state, formed in FP64 and
@@ -177,7 +233,9 @@ __device__ __forceinline__ void seed_state(const float* sd, double R0, float cha
     s.my = (float)(ty - (double)s.ty);
     s.tz = (float)tz;
     s.mz = (float)(tz - (double)s.tz);
-    s.lam = (float)((double)charge_dir * KAPPA_D / p);
+    const double lam = (double)charge_dir * KAPPA_D / p;
+    s.lam = (float)lam;
+    s.lam_lo = (float)(lam - (double)s.lam);
 }
 
 // Mixed-radix decode of seed `idx` of one grid (row-major over theta0, z0,

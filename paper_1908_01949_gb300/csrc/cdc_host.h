@@ -23,6 +23,13 @@ struct Workspace {
     int n_wires = 0;
 };
 
+// Optional CUDA-event pairs recorded around each scan-kernel launch.
+struct KernelTimer {
+    cudaEvent_t* ev = nullptr;  // [cap]: start, end, start, end, ...
+    int cap = 0;
+    int* used = nullptr;
+};
+
 struct ScanLaunch {
     int n_events;
     const int32_t* hit_off;
@@ -39,6 +46,7 @@ struct ScanLaunch {
     uint32_t* flags;
     unsigned long long* steps;
     int n_rounds, n_zoom;
+    KernelTimer timer;
 };
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.
@@ -68,6 +76,7 @@ struct RefineLaunch {
     int n_seeds;
     const int32_t* seed_event;
     const float* seeds;
+    int n_events;
     const int32_t* hit_off;
     const int32_t* wire_id;
     const float* drift;
@@ -82,6 +91,6 @@ struct RefineLaunch {
     uint32_t* flags;
 };
 cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& P, const RefineLaunch& L,
-                          cudaStream_t st);
+                          float* drift_tab, int num_sms, int do_gn, cudaStream_t st);
 
 }  // namespace cdc

@@ -10,7 +10,24 @@
 namespace cdc {
 
 constexpr int HOUGH_HITS = 64;      // hits staged per block iteration
-constexpr int PEAK_LIST = 2048;     // peak candidates kept before sorting
+constexpr int PEAK_LIST = 2048;     // sorted list of selected peaks (only overflows for counts >= PEAK_HIST)
+constexpr int PEAK_HIST = 2048;     // histogram of peak counts
+
+// Strict local maximum of the 3x3 neighbourhood; an equal neighbour with a
+// lower linear index wins.
+__device__ __forceinline__ bool is_peak(const int32_t* A, int nb, long long c, int v) {
+    const int ix = (int)(c % nb), iy = (int)(c / nb);
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (!dx && !dy) continue;
+            const int x = ix + dx, y = iy + dy;
+            if (x < 0 || y < 0 || x >= nb || y >= nb) continue;
+            const long long n = (long long)y * nb + x;
+            const int vn = A[n];
+            if (vn > v || (vn == v && n < c)) return false;
+        }
+    return true;
+}
 
 // Exact floor(a / b) for 0 <= a < 2^30, b > 0, from a float estimate.
 __device__ __forceinline__ int div_floor(int a, int b, float inv_b) {
@@ -79,7 +96,9 @@ __global__ void __launch_bounds__(1024) hough_peaks_kernel(const int32_t* __rest
                                                            const int32_t* __restrict__ acc, cdc_candidate* cand,
                                                            int32_t* n_cand, cdc_grid* grid_out, uint32_t* flags) {
     __shared__ unsigned long long s_list[PEAK_LIST];
-    __shared__ int s_n, s_max;
+    __shared__ int s_hist2[PEAK_HIST];
+    __shared__ int s_wcnt[32];
+    __shared__ int s_n, s_max, s_t, s_found, s_chunk;
     __shared__ int s_hist[256];
     __shared__ int s_rbin[64];
     const int e = blockIdx.x;
@@ -97,33 +116,82 @@ __global__ void __launch_bounds__(1024) hough_peaks_kernel(const int32_t* __rest
     if ((threadIdx.x & 31) == 0) atomicMax(&s_max, mx);
     __syncthreads();
     const int thr = max(H.min_peak, (s_max + 1) / 2);
+    // Exact selection of the max_cand best peaks without a bound on how many
+    // peaks the accumulator holds: a histogram of peak counts gives the count
+    // t of the last selected peak; peaks above t are collected directly (fewer
+    // than max_cand), peaks equal to t in increasing cell order until the list
+    // is full.
+    for (int b = threadIdx.x; b < PEAK_HIST; b += blockDim.x) s_hist2[b] = 0;
+    __syncthreads();
     for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
         const int v = A[c];
-        if (v < thr || v == 0) continue;
-        const int ix = (int)(c % nb), iy = (int)(c / nb);
-        bool peak = true;
-        for (int dy = -1; dy <= 1 && peak; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (!dx && !dy) continue;
-                const int x = ix + dx, y = iy + dy;
-                if (x < 0 || y < 0 || x >= nb || y >= nb) continue;
-                const long long n = (long long)y * nb + x;
-                const int vn = A[n];
-                if (vn > v || (vn == v && n < c)) {
-                    peak = false;
-                    break;
-                }
-            }
-        if (!peak) continue;
-        const int pos = atomicAdd(&s_n, 1);
-        if (pos < PEAK_LIST) s_list[pos] = ((unsigned long long)(0xffffffffu - (unsigned)v) << 32) | (unsigned)c;
+        if (v >= thr && is_peak(A, nb, c, v)) atomicAdd(&s_hist2[min(v, PEAK_HIST - 1)], 1);
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        int cum = 0, t = -1, lowest = -1;
+        for (int b = PEAK_HIST - 1; b >= 0; --b) {
+            if (s_hist2[b] == 0) continue;
+            lowest = b;
+            cum += s_hist2[b];
+            if (cum >= H.max_cand) {
+                t = b;
+                break;
+            }
+        }
+        s_t = t >= 0 ? t : lowest;  // fewer peaks than max_cand: take them all
+    }
+    __syncthreads();
+    const int t_last = s_t;
+    if (t_last >= 0) {
+        const bool top = t_last == PEAK_HIST - 1;
+        for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int v = A[c];
+            if ((top ? v >= t_last : v > t_last) && is_peak(A, nb, c, v)) {
+                const int pos = atomicAdd(&s_n, 1);
+                if (pos < PEAK_LIST)
+                    s_list[pos] = ((unsigned long long)(0xffffffffu - (unsigned)v) << 32) | (unsigned)c;
+            }
+        }
+        __syncthreads();
+        if (!top) {
+            const int need = H.max_cand - s_n;  // ties at t_last, lowest cell index first
+            if (threadIdx.x == 0) s_found = 0;
+            __syncthreads();
+            for (long long base = 0; base < ncell && s_found < need; base += blockDim.x) {
+                const long long c = base + threadIdx.x;
+                const bool tie = c < ncell && A[c] == t_last && is_peak(A, nb, c, t_last);
+                const unsigned m = __ballot_sync(0xffffffffu, tie);
+                if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = __popc(m);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int acc2 = 0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                        const int k = s_wcnt[w];
+                        s_wcnt[w] = acc2;
+                        acc2 += k;
+                    }
+                    s_chunk = acc2;
+                }
+                __syncthreads();
+                if (tie) {
+                    const int pos = s_found + s_wcnt[threadIdx.x >> 5] + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+                    if (pos < need)
+                        s_list[s_n + pos] = ((unsigned long long)(0xffffffffu - (unsigned)t_last) << 32) | (unsigned)c;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) s_found += s_chunk;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) s_n += min(s_found, need);
+            __syncthreads();
+        }
+    }
     const int np = min(s_n, PEAK_LIST);
     if (threadIdx.x == 0 && s_n > PEAK_LIST) atomicOr(&flags[e], CDC_FLAG_FOUND_OVERFLOW);
     for (int i = np + threadIdx.x; i < PEAK_LIST; i += blockDim.x) s_list[i] = ~0ull;
     __syncthreads();
-    // bitonic sort of the peak keys: (count desc, index asc)
+    // bitonic sort of the selected peak keys: (count desc, index asc)
     for (int k = 2; k <= PEAK_LIST; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < PEAK_LIST; i += blockDim.x) {

@@ -144,15 +144,17 @@ struct ScanIO {
 // steps; a lane whose seed ended takes a new one at the next chunk boundary,
 // so lanes stay busy although seeds end after very different step counts.
 template <int KIND>
-__global__ void __launch_bounds__(256) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+__global__ void __launch_bounds__(256, 3) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
+    __shared__ float4 s_cand[LIST_CAP][256];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
     const long long total = (long long)io.counters[1];
     const int lane = threadIdx.x & 31;
-    Tracer<KIND, false> T;
+    Tracer<KIND> T;
+    FoundList FL;
     long long my = -1;  // -1: wants a seed, -2: no seeds left
     int ev = 0;
     unsigned long long nsteps = 0;
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(256) scan_kernel(DevGeom G, DevField F, ScanCo
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
                     event_seed(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
-                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * G.n_wires, sd);
+                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * G.n_wires, &s_cand[0][threadIdx.x], 256, sd,
+                           FL);
                 } else {
                     my = -2;
                 }
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(256) scan_kernel(DevGeom G, DevField F, ScanCo
         if (__all_sync(FULL, my == -2)) break;
         if (my >= 0) {
             for (int it = 0; it < 16; ++it) {
-                if (!T.step(G, F, P, s_lay, s_tab)) {
+                if (!T.step(G, F, P, s_lay, s_tab, FL)) {
                     int H = io.hit_off[ev + 1] - io.hit_off[ev];
                     io.E[my] = T.score(P, H);
                     if (T.flags) atomicOr(&io.flags[ev], T.flags);
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(256) scan_kernel(DevGeom G, DevField F, ScanCo
                     my = -1;
                     break;
                 }
+                if ((it % LIST_M) == LIST_M - 1) T.rebuild(G, P, s_lay, s_tab);  // seeds start at chunk starts
             }
         }
     }
@@ -361,6 +365,7 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
                                                      float* hit_res2) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
+    __shared__ float4 s_cand[LIST_CAP][128];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
@@ -380,22 +385,23 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
         }
         return;
     }
-    Tracer<KIND, true> T;
-    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * G.n_wires, sd);
-    while (T.step(G, F, P, s_lay, s_tab)) {
-    }
+    Tracer<KIND> T;
+    FoundList FL;
+    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * G.n_wires, &s_cand[0][threadIdx.x], 128, sd, FL);
+    while (T.step(G, F, P, s_lay, s_tab, FL))
+        if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
     for (int h = h0; h < h1; ++h) {
         int w = wire_id[h];
         int part = -1;
         float r2 = P.lam;
-        T.lookup(w, part, r2);
+        found_lookup(FL, T.nf, w, part, r2);
         if (hit_part) hit_part[h] = (int8_t)part;
         if (hit_res2) hit_res2[h] = r2;
     }
 }
 
 // ------------------------------------------------------------ propagation
-template <int KIND>
+template <int KIND, bool LAM2>
 __global__ void propagate_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds, const float* __restrict__ seeds,
                                  int every, int n_rec, double* pos, int32_t* n_steps, double* path) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -409,7 +415,7 @@ __global__ void propagate_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds
     bool outside = true;
     for (;;) {
         if (n >= P.max_steps) break;
-        rkn_step<KIND>(F, s, P.h);
+        rkn_step<KIND, LAM2>(F, s, P.h, P.h6_lo);
         ++n;
         if (n % every == 0 && n / every <= n_rec) {
             double* o = pos + ((size_t)i * n_rec + (n / every - 1)) * 3;
@@ -566,11 +572,18 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
         const long long cap = (r == 0 && L.E0) ? (1ll << 62) : W.e_cap;
         prologue_kernel<<<1, 1024, 0, st>>>(ne, grids, gpe, cap, W.seg_cap, W.seed_off, W.seg_off, W.counters,
                                             L.flags);
-        ScanIO io{W.drift_tab, L.hit_off, grids, gpe, W.seed_off, ne, W.counters, E, L.flags, L.steps};
+        ScanIO io{W.drift_tab, L.hit_off, grids, gpe, W.seed_off, ne, W.counters, E, L.flags,
+                  L.steps ? L.steps + r : nullptr};
+        const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
+        if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
         if (F.kind == 0)
             scan_kernel<0><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
         else
             scan_kernel<1><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
+        if (timed) {
+            cudaEventRecord(L.timer.ev[*L.timer.used + 1], st);
+            *L.timer.used += 2;
+        }
         topk_partial_kernel<<<num_sms * 2, 256, 0, st>>>(E, W.seed_off, W.seg_off, ne, W.counters, P.k, W.seg_keys);
         uint64_t* rk = W.round_keys + (size_t)(r & 1) * W.max_events * CDC_MAX_K;
         topk_merge_kernel<<<blocks_for((long long)ne * 32, 256), 256, 0, st>>>(W.seg_off, ne, P.k, W.seg_keys, rk);
@@ -595,9 +608,14 @@ cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanCons
     const int bs = 128, nb = blocks_for(n_seeds, bs);
     if (precision == 0) {
         if (F.kind == 0)
-            propagate_kernel<0><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+            propagate_kernel<0, false><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
         else
-            propagate_kernel<1><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+            propagate_kernel<1, false><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+    } else if (precision == 2) {
+        if (F.kind == 0)
+            propagate_kernel<0, true><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
+        else
+            propagate_kernel<1, true><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);
     } else {
         if (F.kind == 0)
             propagate_fp64_kernel<0><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, every, n_rec, pos, n_steps, path);

@@ -1,50 +1,179 @@
 // Per-seed track tracer of the scan (arXiv:1908.01949 sec. 2.2, Eq. 1):
 // RKN propagation with turn-partition bookkeeping and track-centric scoring.
 //
-// After every step (segment from state j to j+1) the tracer looks up the
-// fired wires near the new position: the sense layers whose band contains the
-// point (a per-millimetre table of candidate layers plus an exact test against
-// the stereo hyperboloid r_l(z)^2 = R_l^2 + z^2 tan^2 a_l), and in each such
-// layer the cells whose stereo-corrected azimuth lies within the search
-// window.  For a fired wire the derivative of the squared distance to the
-// wire line, g = (r - m)_perp . t, is evaluated at both ends of the segment; a
-// sign change from - to + brackets a local minimum of the distance, which
-// Newton iterations on the cubic Hermite interpolant of the segment locate.
-// The window and band (host-computed) cover every wire whose distance of
-// closest approach can enter Eq. 1 below the cutoff, so the result equals the
-// brute-force definition.  Track ends count as minima when the distance is
-// still decreasing there.
+// Wire search.  Every LIST_M steps the tracer looks up the fired wires near
+// the current point: the sense layers whose band contains the point (a
+// per-millimetre table of candidate layers plus an exact test against the
+// stereo hyperboloid r_l(z)^2 = R_l^2 + z^2 tan^2 a_l), and in each such layer
+// the cells whose stereo-corrected azimuth lies within the search window.  The
+// window is widened by LIST_M h so that it also covers the next LIST_M
+// segments.  Of these wires only the ones the track approaches are kept (a
+// short per-seed list in shared memory): near a wire the squared distance
+// along the track is convex (its second derivative 2(|t_perp|^2 + w_perp .
+// t'_perp) stays positive while |t_perp|^2 exceeds the window radius over the
+// radius of curvature), so a receding wire cannot pass a minimum before the
+// next rebuild; for tracks nearly parallel to the wires receding wires are kept
+// too.  Each step then evaluates, for the listed wires only, the derivative of
+// the squared distance to the wire line, g = (r - m)_perp . t, at the new
+// state; a sign change from - to + brackets a local minimum of the distance,
+// which Newton iterations on the cubic Hermite interpolant of the segment
+// locate.  The window and band (host-computed) cover every wire whose distance
+// of closest approach can enter Eq. 1 below the cutoff, so the result equals
+// the brute-force definition.  Track ends count as minima when the distance is
+// still decreasing there.  If a list overflows, the tracer searches the window
+// at every step until the next rebuild.
+//
+// Layout: every scalar of the tracer lives in registers; the list lives in
+// shared memory ([LIST_CAP][block] layout), the per-seed record of wires scored
+// below lambda (written a few times per seed) in local memory.
 #pragma once
 
 #include "cdc_dev.cuh"
 
 namespace cdc {
 
-template <int KIND, bool KEEP_PART>
+constexpr int LIST_M = 4;              // steps between rebuilds of the candidate list
+constexpr int LIST_CAP = 8;            // candidate wires per seed
+constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
+
+// Wires scored below lambda by one seed: wire | partition << 16, and res^2.
+struct FoundList {
+    uint32_t key[CDC_MAX_FOUND];
+    float r2[CDC_MAX_FOUND];
+};
+
+// Visits the fired wires in the search window (half widths band [mm] in
+// radius and d_win [mm] along the layer) around (rho, phi, z): fn(wire, drift, cosa).
+template <class Fn>
+__device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2* s_tab, const float* dtab,
+                                             float max_drift, float band, float d_win, float rho, float phi, float z,
+                                             Fn&& fn) {
+    const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
+    if (lr.x > lr.y) return;
+    const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
+    const float blo2 = blo * blo, bhi2 = bhi * bhi, z2 = z * z;
+    for (int l = lr.x; l <= lr.y; ++l) {
+        const DevLayer& L = s_lay[l];
+        const float rl2 = fmaf(z2, L.tan2a, L.R2);
+        if (rl2 > bhi2 || rl2 < blo2) continue;
+        const float zt = z * L.tana_over_R, zt2 = zt * zt;
+        // stereo twist atan(z tan(a) / R) by its Taylor series (|zt| < 0.2)
+        const float tw = zt * fmaf(zt2, fmaf(zt2, fmaf(zt2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
+        const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
+        if (!(fabsf(c) < 1.0e6f)) continue;  // non-finite state: nothing to look up
+        const float w = d_win * L.cells_per_mm;
+        const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
+        for (int i = i0; i <= i1; ++i) {
+            int ii = i;  // |c| stays near N/2 at most: a few wraps at worst
+            while (ii < 0) ii += L.N;
+            while (ii >= L.N) ii -= L.N;
+            const int wire = L.base + ii;
+            const float d = __ldg(dtab + wire);
+            if (d <= max_drift) fn(wire, d, L.cosa);
+        }
+    }
+}
+
+// Distance of closest approach inside a segment whose squared-distance
+// derivative changes sign from g0 < 0 to g1 >= 0: Newton iterations on the
+// cubic Hermite interpolant P(u) = r_j + H10 h t_j + H01 (r_j+1 - r_j) +
+// H11 h t_j+1 (u = tau h), started at the root of the linear interpolation of
+// the derivative.  (ax, ay, az) = r_j - m; (Dx, Dy, Dz) = r_j+1 - r_j.  Kept
+// out of line: it runs for a few percent of the steps and would otherwise set
+// the register budget of the whole stepping loop.
+static __device__ __noinline__ float seg_doca(float ax, float ay, float az, float otx, float oty, float otz,
+                                              float Dx, float Dy, float Dz, float ntx, float nty, float ntz,
+                                              float4 W, float cosa, float g0, float g1, float h) {
+    const float ih = 1.0f / h;
+    float u = h * (g0 / (g0 - g1));
+    float wx, wy, wz, wd;
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        const float t = u * ih, t2 = t * t;
+        const float h10 = h * t * fmaf(t, t - 2.0f, 1.0f), h01 = t2 * fmaf(-2.0f, t, 3.0f), h11 = h * t2 * (t - 1.0f);
+        wx = fmaf(h11, ntx, fmaf(h01, Dx, fmaf(h10, otx, ax)));
+        wy = fmaf(h11, nty, fmaf(h01, Dy, fmaf(h10, oty, ay)));
+        wz = fmaf(h11, ntz, fmaf(h01, Dz, fmaf(h10, otz, az)));
+        const float d10 = fmaf(3.0f * t, t, fmaf(-4.0f, t, 1.0f)), d01 = 6.0f * t * (1.0f - t) * ih,
+                    d11 = t * fmaf(3.0f, t, -2.0f);
+        const float vx = fmaf(d11, ntx, fmaf(d01, Dx, d10 * otx));
+        const float vy = fmaf(d11, nty, fmaf(d01, Dy, d10 * oty));
+        const float vz = fmaf(d11, ntz, fmaf(d01, Dz, d10 * otz));
+        const float e10 = fmaf(6.0f, t, -4.0f) * ih, e01 = fmaf(-12.0f, t, 6.0f) * ih * ih,
+                    e11 = fmaf(6.0f, t, -2.0f) * ih;
+        const float ax2 = fmaf(e11, ntx, fmaf(e01, Dx, e10 * otx));
+        const float ay2 = fmaf(e11, nty, fmaf(e01, Dy, e10 * oty));
+        const float az2 = fmaf(e11, ntz, fmaf(e01, Dz, e10 * otz));
+        wd = fmaf(wx, W.z, fmaf(wy, W.w, wz * cosa));
+        const float vd = fmaf(vx, W.z, fmaf(vy, W.w, vz * cosa));
+        const float ad2 = fmaf(ax2, W.z, fmaf(ay2, W.w, az2 * cosa));
+        const float num = fmaf(wx, vx, fmaf(wy, vy, wz * vz)) - wd * vd;
+        const float den =
+            fmaf(vx, vx, fmaf(vy, vy, vz * vz)) - vd * vd + (fmaf(wx, ax2, fmaf(wy, ay2, wz * az2)) - wd * ad2);
+        if (den > 0.f) u = fminf(fmaxf(u - num / den, 0.f), h);
+    }
+    const float t = u * ih, t2 = t * t;
+    const float h10 = h * t * fmaf(t, t - 2.0f, 1.0f), h01 = t2 * fmaf(-2.0f, t, 3.0f), h11 = h * t2 * (t - 1.0f);
+    wx = fmaf(h11, ntx, fmaf(h01, Dx, fmaf(h10, otx, ax)));
+    wy = fmaf(h11, nty, fmaf(h01, Dy, fmaf(h10, oty, ay)));
+    wz = fmaf(h11, ntz, fmaf(h01, Dz, fmaf(h10, otz, az)));
+    wd = fmaf(wx, W.z, fmaf(wy, W.w, wz * cosa));
+    const float px = wx - wd * W.z, py = wy - wd * W.w, pz = wz - wd * cosa;
+    return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+}
+
+// Derivative of the squared distance to the wire line along the track, and
+// |t_perp|^2, at point r with direction t.
+__device__ __forceinline__ float dist_slope(float rx, float ry, float rz, float tx, float ty, float tz, float4 W,
+                                            float cosa, float& tperp2) {
+    const float ax = rx - W.x, ay = ry - W.y;
+    const float ad = fmaf(ax, W.z, fmaf(ay, W.w, rz * cosa));
+    const float td = fmaf(tx, W.z, fmaf(ty, W.w, tz * cosa));
+    tperp2 = fmaf(-td, td, fmaf(tx, tx, fmaf(ty, ty, tz * tz)));
+    return fmaf(ax, tx, fmaf(ay, ty, rz * tz)) - ad * td;
+}
+
+__device__ __forceinline__ float point_doca(float rx, float ry, float rz, float4 W, float cosa) {
+    const float ax = rx - W.x, ay = ry - W.y;
+    const float ad = fmaf(ax, W.z, fmaf(ay, W.w, rz * cosa));
+    const float px = ax - ad * W.z, py = ay - ad * W.w, pz = rz - ad * cosa;
+    return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+}
+
+__device__ __forceinline__ float rho_of(float x, float y) {
+    const float r2 = fmaf(x, x, y * y);
+    return r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+}
+
+__device__ __forceinline__ bool in_chamber(const uchar2* s_tab, float rho) {
+    const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
+    return lr.x <= lr.y;
+}
+
+template <int KIND>
 struct Tracer {
     State s;
     const float* dtab;
-    int n, part;
-    bool outside;
+    float4* cand;   // this thread's list column: cand[k * stride] = (wire bits, g, drift, cosa)
+    int stride;
+    int n, part, nf, nc;
+    bool outside, over;
     float eacc;
-    int nf;
     unsigned long long bloom;
     uint32_t flags;
-    uint32_t fkey[CDC_MAX_FOUND];  // wire | partition << 16
-    float fr2[CDC_MAX_FOUND];
 
     // Best squared residual of `wire` below lambda; Eq. 1 accumulates
     // min(res^2, lambda) - lambda on top of H lambda.
-    __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r2) {
+    __device__ __forceinline__ void found(const ScanConst& P, FoundList& FL, int wire, int pt, float r2) {
         if (!(r2 < P.lam)) return;
         const unsigned long long bit = 1ull << (wire & 63);
         if (bloom & bit) {
             for (int i = 0; i < nf; ++i) {
-                if ((int)(fkey[i] & 0xffffu) == wire) {
-                    if (r2 < fr2[i]) {
-                        eacc += r2 - fr2[i];
-                        fr2[i] = r2;
-                        fkey[i] = (uint32_t)wire | ((uint32_t)pt << 16);
+                if ((int)(FL.key[i] & 0xffffu) == wire) {
+                    if (r2 < FL.r2[i]) {
+                        eacc += r2 - FL.r2[i];
+                        FL.r2[i] = r2;
+                        FL.key[i] = (uint32_t)wire | ((uint32_t)pt << 16);
                     }
                     return;
                 }
@@ -53,151 +182,108 @@ struct Tracer {
         bloom |= bit;
         eacc += r2 - P.lam;
         if (nf < CDC_MAX_FOUND) {
-            fkey[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
-            fr2[nf] = r2;
+            FL.key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
+            FL.r2[nf] = r2;
             ++nf;
         } else {
             flags |= CDC_FLAG_FOUND_OVERFLOW;
         }
     }
 
-    __device__ __forceinline__ void lookup(int wire, int& pt, float& r2) const {
-        for (int i = 0; i < nf; ++i)
-            if ((int)(fkey[i] & 0xffffu) == wire) {
-                pt = (int)(fkey[i] >> 16);
-                r2 = fr2[i];
-            }
-    }
-
-    // Calls fn(wire, drift, cosa) for every fired wire in the search window
-    // around (x, y, z); returns rho.
-    template <class Fn>
-    __device__ __forceinline__ float for_window(const ScanConst& P, const DevLayer* s_lay, const uchar2* s_tab,
-                                                float x, float y, float z, Fn&& fn) const {
-        const float rho = sqrtf(fmaf(x, x, y * y));
-        const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
-        if (lr.x <= lr.y) {
-            const float phi = atan2f(y, x);
-            const float blo = fmaxf(rho - P.band, 0.f), bhi = rho + P.band;
-            const float blo2 = blo * blo, bhi2 = bhi * bhi;
-            for (int l = lr.x; l <= lr.y; ++l) {
-                const DevLayer& L = s_lay[l];
-                const float rl2 = fmaf(z * z, L.tan2a, L.R2);
-                if (rl2 > bhi2 || rl2 < blo2) continue;
-                const float zt = z * L.tana_over_R;
-                const float z2 = zt * zt;
-                // stereo twist atan(z tan(a) / R) by its Taylor series (|zt| < 0.2 for any allowed stereo angle)
-                const float tw = zt * fmaf(z2, fmaf(z2, fmaf(z2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
-                const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
-                if (!(fabsf(c) < 1.0e6f)) continue;  // non-finite state: nothing to look up
-                const float w = P.d_win * L.cells_per_mm;
-                const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
-                for (int i = i0; i <= i1; ++i) {
-                    int ii = i % L.N;
-                    if (ii < 0) ii += L.N;
-                    const int wire = L.base + ii;
-                    const float d = __ldg(dtab + wire);
-                    if (!(d <= P.max_drift)) continue;
-                    fn(wire, d, L.cosa);
-                }
-            }
-        }
-        return rho;
+    // Candidate list for the next LIST_M segments, built at the current state.
+    __device__ __forceinline__ void rebuild(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                            const uchar2* s_tab) {
+        nc = 0;
+        over = false;
+        const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
+        const float rho = rho_of(x, y);
+        if (!in_chamber(s_tab, rho)) return;
+        const float wide = LIST_M * P.h;
+        visit_window(s_lay, s_tab, dtab, P.max_drift, P.band + wide, P.d_win + wide, rho, atan2f(y, x), z,
+                     [&](int wire, float d, float cosa) {
+                         const float4 W = __ldg(G.wires + wire);
+                         float tp2;
+                         const float g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
+                         if (g < 0.f || tp2 < PARALLEL_T2) {
+                             if (nc < LIST_CAP) {
+                                 cand[nc * stride] = make_float4(__int_as_float(wire), g, d, cosa);
+                                 ++nc;
+                             } else {
+                                 over = true;
+                             }
+                         }
+                     });
     }
 
     __device__ __forceinline__ void init(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
-                                         const uchar2* s_tab, const float* dtab_, const float* sd) {
+                                         const uchar2* s_tab, const float* dtab_, float4* cand_, int stride_,
+                                         const float* sd, FoundList& FL) {
         seed_state(sd, G.R0d, P.charge_dir, P.direction, s);
         dtab = dtab_;
+        cand = cand_;
+        stride = stride_;
         n = 0;
         part = 0;
-        outside = true;
-        eacc = 0.f;
         nf = 0;
+        nc = 0;
+        outside = true;
+        over = false;
+        eacc = 0.f;
         bloom = 0ull;
         flags = 0u;
         // start of the track: a minimum if the distance grows from there
         const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
-        for_window(P, s_lay, s_tab, x, y, z, [&](int wire, float d, float cosa) {
-            const float4 W = __ldg(G.wires + wire);
-            const float ax = x - W.x, ay = y - W.y, az = z;
-            const float ad = fmaf(ax, W.z, fmaf(ay, W.w, az * cosa));
-            const float td = fmaf(tx, W.z, fmaf(ty, W.w, tz * cosa));
-            const float g = fmaf(ax, tx, fmaf(ay, ty, az * tz)) - ad * td;
-            if (g > 0.f) {
-                const float px = ax - ad * W.z, py = ay - ad * W.w, pz = az - ad * cosa;
-                const float D = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
-                const float r = D - d;
-                found(P, wire, 0, r * r);
-            }
-        });
+        const float rho = rho_of(x, y);
+        if (in_chamber(s_tab, rho))
+            visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(y, x), z,
+                         [&](int wire, float d, float cosa) {
+                             const float4 W = __ldg(G.wires + wire);
+                             float tp2;
+                             if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f) {
+                                 const float r = point_doca(x, y, z, W, cosa) - d;
+                                 found(P, FL, wire, 0, r * r);
+                             }
+                         });
+        rebuild(G, P, s_lay, s_tab);
     }
 
+    // One RKN step and the minima inside the new segment; false once the track ended.
     __device__ __forceinline__ bool step(const DevGeom& G, const DevField& F, const ScanConst& P,
-                                         const DevLayer* s_lay, const uchar2* s_tab) {
+                                         const DevLayer* s_lay, const uchar2* s_tab, FoundList& FL) {
         const float ox = s.rx, oy = s.ry, oz = s.rz, otx = s.tx, oty = s.ty, otz = s.tz;
-        rkn_step<KIND>(F, s, P.h);
+        rkn_step<KIND>(F, s, P.h, P.h6_lo);
         ++n;
         const float nx = s.rx, ny = s.ry, nz = s.rz, ntx = s.tx, nty = s.ty, ntz = s.tz;
+        const float rho = rho_of(nx, ny);
         const int pt = part;
-        const float h = P.h, ih = 1.0f / P.h;
-        const float rho = for_window(P, s_lay, s_tab, nx, ny, nz, [&](int wire, float d, float cosa) {
-            const float4 W = __ldg(G.wires + wire);
-            const float ax = ox - W.x, ay = oy - W.y, az = oz;
-            const float ad = fmaf(ax, W.z, fmaf(ay, W.w, az * cosa));
-            const float t0d = fmaf(otx, W.z, fmaf(oty, W.w, otz * cosa));
-            const float g0 = fmaf(ax, otx, fmaf(ay, oty, az * otz)) - ad * t0d;
-            if (!(g0 < 0.f)) return;
-            const float bx = nx - W.x, by = ny - W.y, bz = nz;
-            const float bd = fmaf(bx, W.z, fmaf(by, W.w, bz * cosa));
-            const float t1d = fmaf(ntx, W.z, fmaf(nty, W.w, ntz * cosa));
-            const float g1 = fmaf(bx, ntx, fmaf(by, nty, bz * ntz)) - bd * t1d;
-            if (g1 < 0.f) return;
-            // local minimum inside the segment: Newton on the Hermite cubic
-            // P(u) = r_j + H10 h t_j + H01 (r_j+1 - r_j) + H11 h t_j+1, u = tau h
-            const float Dx = nx - ox, Dy = ny - oy, Dz = nz - oz;
-            float u = h * (g0 / (g0 - g1));
-            float wx = 0.f, wy = 0.f, wz = 0.f, wd = 0.f;
-#pragma unroll
-            for (int it = 0; it < 3; ++it) {
-                const float t = u * ih, t2 = t * t;
-                const float h10 = h * t * fmaf(t, t - 2.0f, 1.0f), h01 = t2 * fmaf(-2.0f, t, 3.0f),
-                            h11 = h * t2 * (t - 1.0f);
-                wx = fmaf(h11, ntx, fmaf(h01, Dx, fmaf(h10, otx, ax)));
-                wy = fmaf(h11, nty, fmaf(h01, Dy, fmaf(h10, oty, ay)));
-                wz = fmaf(h11, ntz, fmaf(h01, Dz, fmaf(h10, otz, az)));
-                const float d10 = fmaf(3.0f * t, t, fmaf(-4.0f, t, 1.0f)), d01 = 6.0f * t * (1.0f - t) * ih,
-                            d11 = t * fmaf(3.0f, t, -2.0f);
-                const float vx = fmaf(d11, ntx, fmaf(d01, Dx, d10 * otx));
-                const float vy = fmaf(d11, nty, fmaf(d01, Dy, d10 * oty));
-                const float vz = fmaf(d11, ntz, fmaf(d01, Dz, d10 * otz));
-                const float e10 = fmaf(6.0f, t, -4.0f) * ih, e01 = fmaf(-12.0f, t, 6.0f) * ih * ih,
-                            e11 = fmaf(6.0f, t, -2.0f) * ih;
-                const float ax2 = fmaf(e11, ntx, fmaf(e01, Dx, e10 * otx));
-                const float ay2 = fmaf(e11, nty, fmaf(e01, Dy, e10 * oty));
-                const float az2 = fmaf(e11, ntz, fmaf(e01, Dz, e10 * otz));
-                wd = fmaf(wx, W.z, fmaf(wy, W.w, wz * cosa));
-                const float vd = fmaf(vx, W.z, fmaf(vy, W.w, vz * cosa));
-                const float ad2 = fmaf(ax2, W.z, fmaf(ay2, W.w, az2 * cosa));
-                const float num = fmaf(wx, vx, fmaf(wy, vy, wz * vz)) - wd * vd;
-                const float den = fmaf(vx, vx, fmaf(vy, vy, vz * vz)) - vd * vd +
-                                  (fmaf(wx, ax2, fmaf(wy, ay2, wz * az2)) - wd * ad2);
-                if (den > 0.f) u = fminf(fmaxf(u - num / den, 0.f), h);
+        const float h = P.h;
+        auto seg = [&](int wire, float d, float cosa, float g0, float g1, float4 W) {
+            const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W,
+                                     cosa, g0, g1, h) - d;
+            found(P, FL, wire, pt, r * r);
+        };
+        if (!over) {
+            for (int k = 0; k < nc; ++k) {
+                float4 e = cand[k * stride];
+                const int wire = __float_as_int(e.x);
+                const float4 W = __ldg(G.wires + wire);
+                float tp2;
+                const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, e.w, tp2);
+                if (e.y < 0.f && g1 >= 0.f) seg(wire, e.z, e.w, e.y, g1, W);
+                e.y = g1;
+                cand[k * stride] = e;
             }
-            {
-                const float t = u * ih, t2 = t * t;
-                const float h10 = h * t * fmaf(t, t - 2.0f, 1.0f), h01 = t2 * fmaf(-2.0f, t, 3.0f),
-                            h11 = h * t2 * (t - 1.0f);
-                wx = fmaf(h11, ntx, fmaf(h01, Dx, fmaf(h10, otx, ax)));
-                wy = fmaf(h11, nty, fmaf(h01, Dy, fmaf(h10, oty, ay)));
-                wz = fmaf(h11, ntz, fmaf(h01, Dz, fmaf(h10, otz, az)));
-                wd = fmaf(wx, W.z, fmaf(wy, W.w, wz * cosa));
-            }
-            const float px = wx - wd * W.z, py = wy - wd * W.w, pz = wz - wd * cosa;
-            const float D = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
-            const float r = D - d;
-            found(P, wire, pt, r * r);
-        });
+        } else if (in_chamber(s_tab, rho)) {
+            visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
+                         [&](int wire, float d, float cosa) {
+                             const float4 W = __ldg(G.wires + wire);
+                             float tp2;
+                             const float g0 = dist_slope(ox, oy, oz, otx, oty, otz, W, cosa, tp2);
+                             if (!(g0 < 0.f)) return;
+                             const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2);
+                             if (g1 >= 0.f) seg(wire, d, cosa, g0, g1, W);
+                         });
+        }
         const bool now_out = rho >= G.R0;
         bool stop = false;
         if (outside && !now_out) {
@@ -213,24 +299,35 @@ struct Tracer {
         if (stop && part < P.max_part) {
             // end of the track: a minimum if the distance is still shrinking there
             const int pe = part;
-            for_window(P, s_lay, s_tab, nx, ny, nz, [&](int wire, float d, float cosa) {
+            auto end_min = [&](int wire, float d, float cosa) {
                 const float4 W = __ldg(G.wires + wire);
-                const float ax = nx - W.x, ay = ny - W.y, az = nz;
-                const float ad = fmaf(ax, W.z, fmaf(ay, W.w, az * cosa));
-                const float td = fmaf(ntx, W.z, fmaf(nty, W.w, ntz * cosa));
-                const float g = fmaf(ax, ntx, fmaf(ay, nty, az * ntz)) - ad * td;
-                if (g < 0.f) {
-                    const float px = ax - ad * W.z, py = ay - ad * W.w, pz = az - ad * cosa;
-                    const float D = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
-                    const float r = D - d;
-                    found(P, wire, pe, r * r);
+                float tp2;
+                if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
+                    const float r = point_doca(nx, ny, nz, W, cosa) - d;
+                    found(P, FL, wire, pe, r * r);
                 }
-            });
+            };
+            if (!over) {
+                for (int k = 0; k < nc; ++k) {
+                    const float4 e = cand[k * stride];
+                    if (e.y < 0.f) end_min(__float_as_int(e.x), e.z, e.w);
+                }
+            } else if (in_chamber(s_tab, rho)) {
+                visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz, end_min);
+            }
         }
         return !stop;
     }
 
     __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
 };
+
+__device__ __forceinline__ void found_lookup(const FoundList& FL, int nf, int wire, int& pt, float& r2) {
+    for (int i = 0; i < nf; ++i)
+        if ((int)(FL.key[i] & 0xffffu) == wire) {
+            pt = (int)(FL.key[i] >> 16);
+            r2 = FL.r2[i];
+        }
+}
 
 }  // namespace cdc

@@ -1,0 +1,92 @@
+"""GPU parity of the circle Hough transform (sec. 2.1) and of the ten-round
+zoom re-scan (sec. 2.2) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import cdc_synth as S
+import oracle as O
+from tests.gpu_util import E_REL, MARGIN, check_topk, keys_to_index, oracle_params, tracker
+
+pytestmark = pytest.mark.gpu
+
+
+def test_hough_bit_exact_batched(field_map):
+    """Accumulators and candidate lists of three events in one call are
+    bit-identical to the oracle's; the seed centres agree to float rounding;
+    an event without hits yields no candidate and an empty grid."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    events = [S.cfg2_case(i, field_map)[2] for i in range(3)]
+    empty = S.Event(wire_id=np.zeros(0, np.int32), drift=np.zeros(0, np.float32),
+                    truth_part=np.zeros(0, np.int8), truth_seeds=events[0].truth_seeds, n_turns=1)
+    events.insert(1, empty)
+    off, wid, dr = S.pack_events(events)
+    tr = tracker(g, field_map)
+    doff, dwid, _ = tr.events_to_device(off, wid, dr)
+    tmpl = S.cfg2_grid_template()
+    hp = cdc.hough_params(max_cand=6, grid_template=tmpl)
+    out = tr.hough(doff, dwid, hp)
+    torch.cuda.synchronize()
+    acc = out["acc"].cpu().numpy()
+    cand = cdc.decode_candidates(out["cand"]).reshape(len(events), hp.max_cand)
+    ncand = out["n_cand"].cpu().numpy()
+    grids = cdc.tensor_to_grids(out["grid"])
+    flags = out["flags"].cpu().numpy()
+    OH = O.hough_params(max_cand=6)
+    for e, ev in enumerate(events):
+        racc, rc, rcen = O.hough(g, OH, ev.wire_id)
+        assert np.array_equal(acc[e], racc), e
+        assert ncand[e] == rc.shape[0]
+        got = np.stack([cand[e]["ix"], cand[e]["iy"], cand[e]["count"], cand[e]["r_bin"]], 1)[:ncand[e]]
+        assert np.array_equal(got, rc)
+        cen = np.stack([cand[e]["theta0"], cand[e]["px0"], cand[e]["py0"]], 1)[:ncand[e]]
+        assert np.allclose(cen, rcen, rtol=1e-6, atol=1e-5, equal_nan=True)
+        if ncand[e]:
+            assert grids[e]["centre"][0] == np.float32(rcen[0, 0]) or abs(grids[e]["centre"][0] - rcen[0, 0]) < 1e-6
+            assert np.array_equal(grids[e]["n"], tmpl["n"][0])
+    assert ncand[1] == 0 and flags[1] & cdc.FLAG_EMPTY and np.all(grids[1]["n"] == 0)
+
+
+def test_zoom_rounds_follow_oracle_scores():
+    """Round r's grids are 3^5 grids with the coarse step times 2^-r centred on a
+    valid top-n_zoom of round r-1 (by the oracle's scores, ties within
+    tolerance); the reported best score equals the oracle's score of the
+    reported best seed and is not above the coarse best."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, grid = S.cfg1_case(6)
+    n0 = int(np.prod(grid["n"][0]))
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    p = cdc.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1, k=8, n_rounds=10, n_zoom=4)
+    out = tr.scan(off, wid, dr, cdc.grids_to_tensor(grid, tr.dev), p, want_E=True, n_seeds=n0,
+                  want_zoom_grids=True)
+    torch.cuda.synchronize()
+    zg = cdc.tensor_to_grids(out["zoom_grids"]).reshape(10, 1, 4)
+    op = oracle_params(p)
+    drift = ev.drift.astype(np.float64)
+    prev_seeds = O.grid_values(grid)
+    prev_E = O.scan(g, f, ev.wire_id, drift, prev_seeds, op)["E"]
+    coarse_best = prev_E.min()
+    for r in range(1, 10):
+        order = O.topk(prev_E, 4)
+        kth = prev_E[order[-1]]
+        seeds_r = []
+        for c in range(4):
+            gr = zg[r, 0, c]
+            assert np.all(gr["n"] == 3)
+            assert np.allclose(gr["step"], grid["step"][0] * 2.0 ** -r, rtol=1e-7)
+            # the centre is one of the previous round's seeds, with a score among the best 4 up to ties
+            i = np.flatnonzero(np.all(prev_seeds == gr["centre"].astype(np.float64), axis=1))
+            assert i.size >= 1, (r, c)
+            assert prev_E[i[0]] <= kth * (1 + E_REL), (r, c)
+            seeds_r.append(O.grid_values(gr))
+        prev_seeds = np.concatenate(seeds_r)
+        prev_E = O.scan(g, f, ev.wire_id, drift, prev_seeds, op)["E"]
+    best = out["best_seed"][0, 0].cpu().numpy().astype(np.float64)
+    ref = O.scan(g, f, ev.wire_id, drift, best[None], op)["E"][0]
+    bE = out["best_E"][0].cpu().numpy()
+    assert abs(bE[0] - ref) <= E_REL * ref
+    assert bE[0] <= coarse_best * (1 + E_REL)
+    assert np.all(np.diff(bE) >= 0)

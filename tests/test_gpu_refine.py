@@ -1,0 +1,112 @@
+"""GPU parity of the Gauss-Newton refinement and of the adjoint-RKN chi^2
+gradient against the FP64 oracle (tangent gradient), through the C ABI."""
+import numpy as np
+import pytest
+
+import cdc_synth as S
+import oracle as O
+from tests.gpu_util import oracle_params, tracker
+
+pytestmark = pytest.mark.gpu
+SCALE = np.array([1.0, 100.0, 10.0, 10.0, 10.0])
+
+
+def _cases(kind, field_map=None):
+    if kind == "uniform":
+        g, f, ev, grid = S.cfg1_case(7)
+        mp, ms = 1, 1000
+    else:
+        g = S.make_geometry()
+        f = field_map
+        ev = S.cfg2_case(2, field_map, occupancy=0.05)[2]
+        mp, ms = 3, 3500
+    rng = np.random.default_rng(11)
+    truth = ev.truth_seeds[0]          # first turn: the map case follows 2-3 turns
+    sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * (1.0 if kind == "uniform" else 0.3)
+    seeds = [truth + rng.normal(0, 1, 5) * sig for _ in range(8)]
+    return g, f, ev, np.asarray(seeds, np.float32), mp, ms
+
+
+def _oracle_part(g, f, ev, seed, op):
+    out = O.scan(g, f, ev.wire_id, ev.drift.astype(np.float64), seed[None], op, per_hit=True)
+    return out["hit_part"][0], out["hit_margin"][0]
+
+
+@pytest.mark.parametrize("kind", ["uniform", "map"])
+def test_adjoint_gradient_matches_fp64_oracle(kind, field_map):
+    """chi^2 within 1e-4 relative and d chi^2/d seed (adjoint RKN, FP32) within
+    1e-4 relative (scaled parameters) of the FP64 forward-tangent gradient."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, seeds, mp, ms = _cases(kind, field_map)
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    sp = cdc.scan_params(h=2.0, max_steps=ms, lam=4.0, max_partitions=mp)
+    rp = cdc.refine_params(n_iter=0, sigma=0.2, checkpoint=128)
+    se = torch.zeros(len(seeds), dtype=torch.int32, device=tr.dev)
+    out = tr.chi2_grad(se, torch.as_tensor(seeds, device=tr.dev), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    c2 = out["chi2"].cpu().numpy()
+    gr = out["grad"].cpu().numpy()
+    nu = out["n_used"].cpu().numpy()
+    op = oracle_params(sp)
+    checked = 0
+    for i, sd in enumerate(seeds.astype(np.float64)):
+        part, margin = _oracle_part(g, f, ev, sd, op)
+        if (margin < 1e-3).any():
+            continue                      # a hit at a classification cut: the two sides may classify differently
+        rc2, rg, _, rnu, rfl = O.chi2(g, f, op, ev.wire_id, ev.drift.astype(np.float64), part, sd)
+        assert nu[i] == rnu
+        assert abs(c2[i] - rc2) <= 1e-4 * rc2, (i, c2[i], rc2)
+        rel = np.linalg.norm((gr[i] - rg) * SCALE) / np.linalg.norm(rg * SCALE)
+        assert rel <= 1e-4, (i, rel, gr[i], rg)
+        checked += 1
+    assert checked >= 4
+
+
+@pytest.mark.parametrize("kind", ["uniform", "map"])
+def test_gauss_newton_refine_matches_oracle(kind, field_map):
+    """Five Gauss-Newton iterations from the same starting seeds land on the
+    same refined seeds as the FP64 oracle, with the same chi^2."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, seeds, mp, ms = _cases(kind, field_map)
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    sp = cdc.scan_params(h=2.0, max_steps=ms, lam=4.0, max_partitions=mp)
+    rp = cdc.refine_params(n_iter=5, sigma=0.2, checkpoint=128)
+    se = torch.zeros(len(seeds), dtype=torch.int32, device=tr.dev)
+    out = tr.refine(se, torch.as_tensor(seeds, device=tr.dev), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    so = out["seeds"].cpu().numpy().astype(np.float64)
+    c2 = out["chi2"].cpu().numpy()
+    op = oracle_params(sp)
+    checked = 0
+    for i, sd in enumerate(seeds.astype(np.float64)):
+        part, margin = _oracle_part(g, f, ev, sd, op)
+        if (margin < 1e-3).any():
+            continue
+        rso, rc2, rg, rnu, rfl = O.refine(g, f, op, ev.wire_id, ev.drift.astype(np.float64), part, sd, n_iter=5)
+        c0 = O.chi2(g, f, op, ev.wire_id, ev.drift.astype(np.float64), part, sd)[0]
+        if not rc2 < c0:
+            continue                      # the start lies outside the Gauss-Newton basin: no unique answer
+        assert abs(c2[i] - rc2) <= 1e-3 * max(rc2, 1.0), (i, c2[i], rc2)
+        assert np.all(np.abs((so[i] - rso) / SCALE) < 2e-4), (i, so[i], rso)
+        checked += 1
+    assert checked >= 4
+
+
+def test_seed_event_out_of_range_is_flagged():
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, seeds, mp, ms = _cases("uniform")
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    sp = cdc.scan_params(h=2.0, max_steps=ms, lam=4.0, max_partitions=mp)
+    rp = cdc.refine_params(n_iter=1)
+    se = torch.tensor([0, 5], dtype=torch.int32, device=tr.dev)
+    out = tr.refine(se, torch.as_tensor(seeds[:2], device=tr.dev), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    fl = out["flags"].cpu().numpy()
+    assert fl[1] & cdc.FLAG_BAD_HIT and np.isnan(out["chi2"][1].item())
+    assert not (fl[0] & cdc.FLAG_BAD_HIT)
