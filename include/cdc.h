@@ -252,6 +252,36 @@ int cdc_propagate(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_
 int cdc_kernel_timer(cdc_ctx* ctx, int enable);
 int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* per_launch_ms, int cap);
 
+/* ---- allocation-free scan ---------------------------------------------- */
+
+#define CDC_NOALLOC_MAX_EVENTS 8
+#define CDC_NOALLOC_MAX_SEEDS 65536
+
+/* The paper has no counterpart to this call.  It exists for callers that
+ * cannot allocate device memory at call time (an allocator callback that must
+ * not re-enter cudaMalloc, a process whose device memory belongs to another
+ * framework's caching allocator, a real-time loop that forbids allocation
+ * after start-up).  It computes what cdc_scan_seeds computes for a
+ * single-round scan (params->n_rounds must be 1; no zoom rounds), with the
+ * same inputs and outputs, but takes its workspace from a fixed array of
+ * about 0.6 MB that the library keeps in device memory on every device where
+ * it is loaded (until the process exits) instead of from cdc_reserve; it
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ * Limits: n_events <= CDC_NOALLOC_MAX_EVENTS and n_seeds (the number of seeds
+ * the grids hold, stated by the caller) <= CDC_NOALLOC_MAX_SEEDS, else
+ * CDC_ERR_RANGE; if the grids hold more seeds than that on the device, every
+ * event is flagged CDC_FLAG_EMPTY and nothing is scanned.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other's results, so
+ * serialise them.  Errors as cdc_scan_seeds. */
+int cdc_scan_seeds_noalloc(cdc_ctx* ctx, int n_events, int64_t n_seeds, const int32_t* hit_off,
+                           const int32_t* wire_id, const float* drift, const cdc_grid* grids,
+                           const cdc_scan_params* params, float* E, uint64_t* topk0, float* best_E, float* best_seed,
+                           int8_t* hit_part, float* hit_res2, uint32_t* flags, unsigned long long* steps,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 # All entry points of include/cdc.h.
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
-           "cdc_kernel_timer", "cdc_kernel_time"]
+           "cdc_kernel_timer", "cdc_kernel_time", "cdc_scan_seeds_noalloc"]
 
 
 class cdc_grid(C.Structure):
@@ -101,6 +101,8 @@ def lib():
                                     vp, vp, vp, vp, vp]
         L.cdc_propagate.argtypes = [vp, C.c_int, vp, P(cdc_scan_params), C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
         L.cdc_kernel_timer.argtypes = [vp, C.c_int]
+        L.cdc_scan_seeds_noalloc.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp, vp, vp,
+                                             vp, vp, vp, vp]
         L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
         for name in EXPORTS:
             if name not in ("cdc_destroy", "cdc_last_error"):
@@ -277,6 +279,21 @@ class Context:
             _dev(drift, torch.float32, "drift", d), C.byref(scan), C.byref(params),
             _dev(chi2, torch.float64, "chi2", d), _dev(grad, torch.float32, "grad", d, True),
             _dev(n_used, torch.int32, "n_used", d, True), _dev(flags, torch.int32, "flags", d), _stream(stream)))
+
+    def cdc_scan_seeds_noalloc(self, n_events, n_seeds, hit_off, wire_id, drift, grids, params, E, topk0, best_E,
+                               best_seed, hit_part, hit_res2, flags, steps, stream=None):
+        """Single-round scan whose workspace is a fixed device array of the
+        library (for callers that must not allocate device memory)."""
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_scan_seeds_noalloc(
+            self.h, int(n_events), int(n_seeds), _dev(hit_off, torch.int32, "hit_off", d),
+            _dev(wire_id, torch.int32, "wire_id", d), _dev(drift, torch.float32, "drift", d),
+            _dev(grids, torch.uint8, "grids", d), C.byref(params), _dev(E, torch.float32, "E", d, True),
+            _dev(topk0, torch.int64, "topk0", d, True), _dev(best_E, torch.float32, "best_E", d),
+            _dev(best_seed, torch.float32, "best_seed", d), _dev(hit_part, torch.int8, "hit_part", d, True),
+            _dev(hit_res2, torch.float32, "hit_res2", d, True), _dev(flags, torch.int32, "flags", d),
+            _dev(steps, torch.int64, "steps", d, True), _stream(stream)))
 
     def cdc_kernel_timer(self, enable):
         return self._check(self.L.cdc_kernel_timer(self.h, int(bool(enable))))

@@ -528,3 +528,25 @@ int cdc_kernel_time(cdc_ctx* c, double* total_ms, int64_t* launches, float* per_
 }
 
 }  // extern "C"
+
+namespace cdc {
+
+// Context view for the allocation-free scan (noalloc.cu): validates the scan
+// parameters exactly as cdc_scan_seeds does and hands out the loaded tables.
+int scan_view(cdc_ctx* c, const cdc_scan_params* p, DevGeom* G, DevField* F, ScanConst* P, int* num_sms,
+              int* device) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    int rc = check_scan_params(c, p, true);
+    if (rc) return rc;
+    *G = c->G;
+    *F = c->F;
+    *P = make_const(c, p);
+    *num_sms = c->num_sms;
+    *device = c->device;
+    return CDC_OK;
+}
+
+int set_error(cdc_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+
+}  // namespace cdc
