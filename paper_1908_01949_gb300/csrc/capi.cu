@@ -32,6 +32,7 @@ struct cdc_ctx {
     // field
     bool field = false;
     DevField F{};
+    float b_max = 0.f;
     float4* d_cells = nullptr;
     // workspace
     Workspace W{};
@@ -118,7 +119,7 @@ int check_scan_params(cdc_ctx* c, const cdc_scan_params* p, bool need_k) {
         if (p->n_rounds > 1 && (p->n_zoom < 1 || p->n_zoom > CDC_MAX_ZOOM || p->n_zoom > p->k))
             return fail(c, CDC_ERR_RANGE, "n_zoom outside 1..min(k, 8)");
     }
-    if (search_width(c, p) + 4.0f * p->h > TAB_BAND)  // the candidate lists widen the window by 4 h
+    if (search_width(c, p) + LIST_M * p->h > TAB_BAND)  // the candidate lists widen the window by LIST_M h
         return fail(c, CDC_ERR_RANGE, "max_drift + sqrt(lambda) (or h) too large for the wire search window");
     return CDC_OK;
 }
@@ -128,10 +129,12 @@ ScanConst make_const(const cdc_ctx* c, const cdc_scan_params* p) {
     P.h = p->h;
     P.h6_lo = (float)((double)p->h / 6.0 - (double)(p->h * (1.0f / 6.0f)));
     P.lam = p->lambda;
+    P.sqrt_lam = sqrtf(p->lambda);
     P.charge_dir = p->charge * (float)p->direction;
     P.band = search_width(c, p);
     P.d_win = P.band;
     P.max_drift = p->max_drift;
+    P.b_max = c->b_max;
     P.max_steps = p->max_steps;
     P.max_part = p->max_partitions;
     P.direction = p->direction;
@@ -279,6 +282,7 @@ int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float*
         c->F = DevField{};
         c->F.kind = 0;
         c->F.B0 = b0;
+        c->b_max = fabsf(b0);
         c->field = true;
         return CDC_OK;
     }
@@ -288,6 +292,8 @@ int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float*
     if (!(dr > 0.f) || !(dz > 0.f) || !(r_min >= 0.f)) return fail(c, CDC_ERR_ARG, "need dr, dz > 0 and r_min >= 0");
     const size_t ncell = (size_t)(nr - 1) * (nz - 1);
     std::vector<float4> cells(2 * ncell);
+    double bmax = 0.0;  // |B| of the bilinear field never exceeds the largest sample norm
+    for (size_t q = 0; q < (size_t)nr * nz; ++q) bmax = std::max(bmax, hypot((double)bz[q], (double)br[q]));
     for (int i = 0; i + 1 < nr; ++i)
         for (int j = 0; j + 1 < nz; ++j) {
             const float* m[2] = {bz, br};
@@ -318,6 +324,7 @@ int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float*
     F.dr = dr;
     F.dz = dz;
     c->F = F;
+    c->b_max = (float)(bmax * (1.0 + 1e-6));
     c->field = true;
     return CDC_OK;
 }

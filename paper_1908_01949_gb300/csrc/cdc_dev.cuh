@@ -13,6 +13,7 @@ constexpr float KAPPA = 0.299792458f;      // MeV/c per (T mm)
 constexpr double KAPPA_D = 0.299792458;
 constexpr int TAB_N = 1024;                // radial candidate-layer table, 1 mm bins
 constexpr float TAB_BAND = 24.0f;          // widest layer band the table supports [mm]
+constexpr int LIST_M = 4;                  // steps between rebuilds of a candidate wire list
 constexpr int SEG = 4096;                  // seeds per top-K segment
 constexpr uint64_t KEY_NONE = ~0ull;       // empty top-K slot
 constexpr int ZOOM_GRID = 243;             // 3^5 seeds per zoom grid
@@ -58,6 +59,8 @@ struct DevField {
 // Scan-call parameters, resolved on the host.
 struct ScanConst {
     float h, h6_lo, lam, charge_dir, band, d_win, max_drift;  // h6_lo = h/6 - float(h/6)
+    float b_max;    // largest |B| of the field [T] (bounds the track curvature)
+    float sqrt_lam; // sqrt(lambda): the residual cut of Eq. 1 as a distance [mm]
     int max_steps, max_part, direction, k;
 };
 

@@ -13,7 +13,9 @@
 // t'_perp) stays positive while |t_perp|^2 exceeds the window radius over the
 // radius of curvature), so a receding wire cannot pass a minimum before the
 // next rebuild; for tracks nearly parallel to the wires receding wires are kept
-// too.  Each step then evaluates, for the listed wires only, the derivative of
+// too.  Approaching wires whose minimum provably lies beyond the list's
+// lifetime (the slope of g is bounded by |t_perp|^2 plus a curvature term)
+// wait for a later list, so lists hold only imminent minima.  Each step then evaluates, for the listed wires only, the derivative of
 // the squared distance to the wire line, g = (r - m)_perp . t, at the new
 // state; a sign change from - to + brackets a local minimum of the distance,
 // which Newton iterations on the cubic Hermite interpolant of the segment
@@ -32,7 +34,6 @@
 
 namespace cdc {
 
-constexpr int LIST_M = 4;              // steps between rebuilds of the candidate list
 constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
@@ -199,12 +200,25 @@ struct Tracer {
         const float rho = rho_of(x, y);
         if (!in_chamber(s_tab, rho)) return;
         const float wide = LIST_M * P.h;
+        // Growth bound of g = w_perp . t (w = r - m) along the track: dg/ds =
+        // |t_perp|^2 + w_perp . t' with |t'| <= |lam| b_max = kap, |w_perp| grows
+        // by at most 1 per mm and |t_perp|^2 by at most 2 kap per mm, so over an
+        // arc s, g rises by at most s (|t_perp|^2 + kap (|w_perp| + 1.5 s)).
+        const float reach = wide + 0.5f;
+        const float kap = fabsf(s.lam) * P.b_max;
         visit_window(s_lay, s_tab, dtab, P.max_drift, P.band + wide, P.d_win + wide, rho, atan2f(y, x), z,
                      [&](int wire, float d, float cosa) {
                          const float4 W = __ldg(G.wires + wire);
                          float tp2;
                          const float g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
-                         if (g < 0.f || tp2 < PARALLEL_T2) {
+                         bool keep = tp2 < PARALLEL_T2;
+                         if (!keep && g < 0.f) {
+                             // a wire whose minimum provably lies beyond the next LIST_M
+                             // steps waits for a later list
+                             const float wp = point_doca(x, y, z, W, cosa);
+                             keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, wp), tp2), g) + 1e-3f >= 0.f;
+                         }
+                         if (keep) {
                              if (nc < LIST_CAP) {
                                  cand[nc * stride] = make_float4(__int_as_float(wire), g, d, cosa);
                                  ++nc;
@@ -257,7 +271,19 @@ struct Tracer {
         const float rho = rho_of(nx, ny);
         const int pt = part;
         const float h = P.h;
+        const float kap = fabsf(s.lam) * P.b_max;
         auto seg = [&](int wire, float d, float cosa, float g0, float g1, float4 W) {
+            // Bounds on the distance of closest approach D before the Newton
+            // search: D <= min(D0, D1), and with D^2' = 2 g and g' >= -kap |w_perp|,
+            // D^2 >= D0^2 + 2 g0 h - kap (D0 + h) h^2 and D^2 >= D1^2 - 2 g1 h -
+            // kap (D1 + h) h^2.  A residual |D - d| provably above sqrt(lambda)
+            // (with 0.01 mm to spare) cannot score.
+            const float D0 = point_doca(ox, oy, oz, W, cosa), D1 = point_doca(nx, ny, nz, W, cosa);
+            const float kh2 = kap * h * h;
+            const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, D0 + h, D0 * D0)),
+                                    fmaf(-2.0f * h, g1, fmaf(-kh2, D1 + h, D1 * D1)));
+            const float hi = d + P.sqrt_lam + 0.01f, lo = d - P.sqrt_lam - 0.01f;
+            if (lb2 > hi * hi || fminf(D0, D1) < lo) return;
             const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W,
                                      cosa, g0, g1, h) - d;
             found(P, FL, wire, pt, r * r);
@@ -307,14 +333,9 @@ struct Tracer {
                     found(P, FL, wire, pe, r * r);
                 }
             };
-            if (!over) {
-                for (int k = 0; k < nc; ++k) {
-                    const float4 e = cand[k * stride];
-                    if (e.y < 0.f) end_min(__float_as_int(e.x), e.z, e.w);
-                }
-            } else if (in_chamber(s_tab, rho)) {
+            // (the list holds only imminent minima, so the end looks at the whole window)
+            if (in_chamber(s_tab, rho))
                 visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz, end_min);
-            }
         }
         return !stop;
     }
