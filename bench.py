@@ -10,6 +10,14 @@ coarse grid plus nine zoom rounds of 4 x 3^5 seeds at halved steps) with up to
 3500 RKN steps of 2 mm and 3 turn partitions -> hit classification of the best
 seed.  Inputs are seeded synthetic events generated on the host.
 
+Refine leg (timed separately, reported beside the scan): the 64 best seeds of
+each of 16 such events (one ten-round scan with k = 64 each) placed in 1024
+event slots (65536 seeds), five Gauss-Newton iterations with forward tangents,
+checkpointed adjoint gradient and the FP64 5x5 solve.
+
+--profile-case shrinks the coarse grid to 240000 seeds (6 pz0 values) for
+profiler captures; its line is marked as such and is not a benchmark result.
+
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 a bounded sample of the same workload instead.
 """
@@ -116,6 +124,64 @@ def make_workload(rank: int):
     return g, fm, ev
 
 
+REFINE_K, REFINE_SLOTS, REFINE_ITER, REFINE_CKPT, REFINE_SIGMA = 64, 1024, 5, 128, 0.2
+
+
+def refine_leg(args, rank, local, g, fm, stream):
+    """Throughput of cdc_refine_seeds on 1024 events x 64 seeds.  The seeds
+    are the 64 best of a ten-round scan of each distinct event; the event
+    slots repeat the distinct events (same hits), so every slot refines the
+    seeds its own scan selected."""
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    n_dist = max(1, int(args.refine_events))
+    evs = [S.cfg2_case(10_000 + 1000 * rank + i, fm, occupancy=0.10)[2] for i in range(n_dist)]
+    tmpl = S.cfg2_grid_template()
+    tr = cdc.Tracker(g, fm, device=local, max_events=REFINE_SLOTS, max_seeds=int(np.prod(tmpl["n"][0])),
+                     max_hits=1 << 20)
+    dev = tr.dev
+    hp = cdc.hough_params(grid_template=tmpl)
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=REFINE_K,
+                         n_rounds=N_ROUNDS, n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    best = []
+    for ev in evs:
+        off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+        h = tr.hough(off, wid, hp, stream=stream)
+        out = tr.scan(off, wid, dr, h["grid"], sp, want_hits=False, stream=stream)
+        best.append(out["best_seed"][0])
+    slot_ev = [evs[i % n_dist] for i in range(REFINE_SLOTS)]
+    hit_off = np.concatenate([[0], np.cumsum([e.wire_id.size for e in slot_ev])]).astype(np.int32)
+    off, wid, dr = tr.events_to_device(hit_off, np.concatenate([e.wire_id for e in slot_ev]),
+                                       np.concatenate([e.drift for e in slot_ev]))
+    seeds = torch.cat([best[i % n_dist] for i in range(REFINE_SLOTS)]).contiguous()
+    seed_event = torch.arange(REFINE_SLOTS, dtype=torch.int32, device=dev).repeat_interleave(REFINE_K)
+    rp = cdc.refine_params(n_iter=REFINE_ITER, sigma=REFINE_SIGMA, checkpoint=REFINE_CKPT)
+    chi0 = tr.chi2_grad(seed_event, seeds, off, wid, dr, sp, rp, want_grad=False, stream=stream)["chi2"]
+    for _ in range(max(1, min(args.warmup, 2))):
+        out = tr.refine(seed_event, seeds, off, wid, dr, sp, rp, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.refine_reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = tr.refine(seed_event, seeds, off, wid, dr, sp, rp, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    c0 = chi0.cpu().numpy()
+    c1 = out["chi2"].cpu().numpy()
+    fl = out["flags"].cpu().numpy()
+    ok = np.isfinite(c0) & np.isfinite(c1) & (c0 > 0)
+    n = int(seeds.shape[0])
+    return {"seeds": n, "events": REFINE_SLOTS, "distinct_events": n_dist, "iterations": REFINE_ITER,
+            "checkpoint": REFINE_CKPT, "ms": ms, "seeds_per_s": n / (ms / 1e3),
+            "events_per_s": REFINE_SLOTS / (ms / 1e3),
+            "median_chi2_ratio": float(np.median(c1[ok] / c0[ok])) if ok.any() else None,
+            "flagged": int((fl != 0).sum()), "timing": f"median of {args.refine_reps} CUDA-event timed calls"}
+
+
 # --------------------------------------------------------------- CUDA arm
 def run_cuda(args, ws, rank, local):
     import torch
@@ -132,6 +198,8 @@ def run_cuda(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     g, fm, ev = make_workload(rank)
     tmpl = S.cfg2_grid_template()
+    if args.profile_case:
+        tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
     seeds_coarse = int(np.prod(tmpl["n"][0]))
     seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
     tr = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
@@ -233,6 +301,9 @@ def run_cuda(args, ws, rank, local):
     h2d = int(off_h.numel() * 4 + wid_h.numel() * 4 + dr_h.numel() * 4)
     d2h = int(out_E.numel() * 4 + out_S.numel() * 4 + out_P.numel() + out_F.numel() * 4)
 
+    refine = None
+    if not args.no_refine and not args.profile_case:
+        refine = refine_leg(args, rank, local, g, fm, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
@@ -250,7 +321,10 @@ def run_cuda(args, ws, rank, local):
         "rkn_steps_per_s": ws * rkn_per_step / (ms / 1e3),
         "coarse_scan": {"launch_ms": statistics.mean(coarse_ms) if coarse_ms else None, "rkn_steps": coarse_steps,
                         "seeds": seeds_coarse},
-        "refine_seeds_per_s": None,
+        "refine_seeds_per_s": refine["seeds_per_s"] if refine else None,
+        "refine": refine,
+        "events_per_s": {"scan": ws / (ms / 1e3),
+                         "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": None, "flops_per_rkn_step": f_step,
@@ -263,6 +337,8 @@ def run_cuda(args, ws, rank, local):
         "wall_s": wall,
         "cpu_baseline": cpu,
     }
+    if args.profile_case:
+        line["config"]["profile_case"] = "240000-seed coarse grid for profiler captures, not a benchmark result"
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -347,6 +423,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seeds", type=int, default=512, help="oracle seeds per step of the reference arm")
+    ap.add_argument("--no-refine", action="store_true", help="skip the refine leg")
+    ap.add_argument("--refine-events", type=int, default=16, help="distinct events of the refine leg")
+    ap.add_argument("--refine-reps", type=int, default=3, help="timed refine calls (median)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -135,7 +135,9 @@ const char* cdc_last_error(const cdc_ctx* ctx);
  * (-sin a sin phi, sin a cos phi, cos a); global wire ids run layer by layer.
  * z_half: active half length; R0: seed cylinder (sec. 2.1); R_out: outer
  * stop radius.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE (n_layers > 64, total
- * wires > 8192, R not increasing, R0 >= R[0]), CDC_ERR_NOMEM. */
+ * wires > 8192, N outside 32..65535, wire pitch below about 2.1 mm, R not
+ * increasing or below 32 mm, |alpha| >= 0.19, R_out above 982 mm),
+ * CDC_ERR_NOMEM. */
 int cdc_load_geometry(cdc_ctx* ctx, int n_layers, const double* R, const double* alpha, const int32_t* N,
                       const double* phi_off, double z_half, double R0, double R_out);
 

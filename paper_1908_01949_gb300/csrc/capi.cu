@@ -189,13 +189,16 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
     if (!R || !alpha || !N || !phi_off) return fail(c, CDC_ERR_ARG, "geometry array is NULL");
     if (n_layers < 1 || n_layers > CDC_MAX_LAYERS) return fail(c, CDC_ERR_RANGE, "n_layers outside 1..64");
     if (!(z_half > 0) || !(R0 > 0) || !(R_out > R0)) return fail(c, CDC_ERR_ARG, "need z_half > 0, 0 < R0 < R_out");
-    if (R_out + TAB_BAND + 10.0 >= TAB_N) return fail(c, CDC_ERR_RANGE, "R_out beyond the radial table (990 mm)");
+    if (R_out + TAB_BAND + 10.0 >= TAB_N) return fail(c, CDC_ERR_RANGE, "R_out + 42 mm beyond the radial table (1024 mm)");
     int nw = 0;
     double tmax = 0.0;
     for (int l = 0; l < n_layers; ++l) {
-        if (N[l] < 3 || N[l] > 65535) return fail(c, CDC_ERR_RANGE, "wires per layer outside 3..65535");
+        if (N[l] < 32 || N[l] > 65535) return fail(c, CDC_ERR_RANGE, "wires per layer outside 32..65535");
+        // a window of half width TAB_BAND spans at most 32 cells of the fired-wire bits
+        if (2.0 * TAB_BAND * (N[l] / (2.0 * PI * (R[l] - TAB_BAND)) * 1.01) > 31.0)
+            return fail(c, CDC_ERR_RANGE, "wire pitch below 2.1 mm: the search window spans more than 32 cells");
         if (!(R[l] > TAB_BAND) || (l > 0 && !(R[l] > R[l - 1])))
-            return fail(c, CDC_ERR_RANGE, "layer radii must increase and exceed 24 mm");
+            return fail(c, CDC_ERR_RANGE, "layer radii must increase and exceed 32 mm");
         if (!(fabs(alpha[l]) < 0.19)) return fail(c, CDC_ERR_RANGE, "|stereo angle| must be below 0.19 rad");
         nw += N[l];
         tmax = std::max(tmax, fabs(tan(alpha[l])));
@@ -205,9 +208,11 @@ int cdc_load_geometry(cdc_ctx* c, int n_layers, const double* R, const double* a
     std::vector<float4> wires(nw);
     std::vector<int2> wum(nw);
     std::vector<float4> wlo(nw);
-    int base = 0;
+    int base = 0, bword = 0;
     for (int l = 0; l < n_layers; ++l) {
         DevLayer& L = lay[l];
+        L.bword = bword;
+        bword += (N[l] >> 5) + 3;
         double ta = tan(alpha[l]);
         L.R2 = (float)(R[l] * R[l]);
         L.tan2a = (float)(ta * ta);
@@ -342,7 +347,7 @@ int cdc_reserve(cdc_ctx* c, int max_events, int64_t max_seeds, int64_t max_hits)
     W.e_cap = std::max<long long>(max_seeds, (long long)max_events * CDC_MAX_ZOOM * ZOOM_GRID);
     W.seg_cap = W.e_cap / SEG + max_events + 1;
     cudaError_t e = cudaSuccess;
-    if ((e = dalloc(W.drift_tab, (size_t)max_events * W.n_wires)) != cudaSuccess ||
+    if ((e = dalloc(W.drift_tab, (size_t)max_events * event_stride(W.n_wires))) != cudaSuccess ||
         (e = dalloc(W.E, (size_t)W.e_cap)) != cudaSuccess || (e = dalloc(W.seed_off, (size_t)max_events + 1)) != cudaSuccess ||
         (e = dalloc(W.seg_off, (size_t)max_events + 1)) != cudaSuccess || (e = dalloc(W.counters, 4)) != cudaSuccess ||
         (e = dalloc(W.seg_keys, (size_t)W.seg_cap * CDC_MAX_K)) != cudaSuccess ||

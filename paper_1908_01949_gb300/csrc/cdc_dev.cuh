@@ -12,8 +12,15 @@ namespace cdc {
 constexpr float KAPPA = 0.299792458f;      // MeV/c per (T mm)
 constexpr double KAPPA_D = 0.299792458;
 constexpr int TAB_N = 1024;                // radial candidate-layer table, 1 mm bins
-constexpr float TAB_BAND = 24.0f;          // widest layer band the table supports [mm]
-constexpr int LIST_M = 4;                  // steps between rebuilds of a candidate wire list
+constexpr float TAB_BAND = 32.0f;          // widest layer band the table supports [mm]
+constexpr int LIST_M = 8;                  // steps between rebuilds of a candidate wire list
+// Per-event hit table: the drift of every wire ([n_wires] floats; a sentinel
+// above any drift where the wire did not fire) followed by FIRED_WORDS words
+// of fired-wire bits, layer by layer: layer l starts at word bword, bit i is
+// wire i, and bits N..N+31 repeat bits 0..31 so that a window of up to 32
+// cells reads two consecutive words without wrapping.
+constexpr int FIRED_WORDS = CDC_MAX_WIRES / 32 + 3 * CDC_MAX_LAYERS;
+__host__ __device__ __forceinline__ size_t event_stride(int n_wires) { return (size_t)n_wires + FIRED_WORDS; }
 constexpr int SEG = 4096;                  // seeds per top-K segment
 constexpr uint64_t KEY_NONE = ~0ull;       // empty top-K slot
 constexpr int ZOOM_GRID = 243;             // 3^5 seeds per zoom grid
@@ -31,7 +38,8 @@ struct DevLayer {
     float cosa_lo;       // cos(alpha) - cosa, the rounding residual
     int N;               // wires in the layer
     int base;            // global id of wire 0
-    int pad2, pad3;
+    int bword;           // first word of the layer's fired bits in the event table
+    int pad3;
 };
 
 // Geometry tables owned by the context (device memory).

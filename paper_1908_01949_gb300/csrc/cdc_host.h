@@ -9,7 +9,7 @@ namespace cdc {
 
 // Device workspace owned by a context, sized by cdc_reserve.
 struct Workspace {
-    float* drift_tab = nullptr;            // [max_events][n_wires]: drift of the fired wire, sentinel if none
+    float* drift_tab = nullptr;            // [max_events][event_stride(n_wires)]: drifts, then fired-wire bits
     float* E = nullptr;                    // [e_cap] scores of the current round
     long long* seed_off = nullptr;         // [max_events + 1]
     int* seg_off = nullptr;                // [max_events + 1]
@@ -50,6 +50,12 @@ struct ScanLaunch {
 };
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.
+
+// Fills the per-event hit tables of n_events events from the CSR hit lists;
+// flags (nullable) receives CDC_FLAG_BAD_HIT for invalid or duplicate hits.
+cudaError_t launch_stage(const DevGeom& G, int n_events, const int32_t* hit_off, const int32_t* wire_id,
+                         const float* drift, float max_drift, float* tab, uint32_t* flags, int num_sms,
+                         cudaStream_t st);
 cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
                         const ScanLaunch& L, int num_sms, cudaStream_t st);
 

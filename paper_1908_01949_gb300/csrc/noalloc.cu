@@ -32,7 +32,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr long long NA_SEG_CAP = CDC_NOALLOC_MAX_SEEDS / SEG + CDC_NOALLOC_MAX_EVENTS + 1;
 constexpr size_t OFF_DRIFT = 0;
-constexpr size_t OFF_E = OFF_DRIFT + align256(sizeof(float) * CDC_NOALLOC_MAX_EVENTS * CDC_MAX_WIRES);
+constexpr size_t OFF_E = OFF_DRIFT + align256(sizeof(float) * CDC_NOALLOC_MAX_EVENTS * (CDC_MAX_WIRES + FIRED_WORDS));
 constexpr size_t OFF_SEEDOFF = OFF_E + align256(sizeof(float) * CDC_NOALLOC_MAX_SEEDS);
 constexpr size_t OFF_SEGOFF = OFF_SEEDOFF + align256(sizeof(long long) * (CDC_NOALLOC_MAX_EVENTS + 1));
 constexpr size_t OFF_COUNT = OFF_SEGOFF + align256(sizeof(int) * (CDC_NOALLOC_MAX_EVENTS + 1));

@@ -27,7 +27,6 @@ namespace cdc {
 
 constexpr int MAX_CK = 64;      // checkpoints per seed
 constexpr int MAX_BLOCK = 256;  // steps between checkpoints
-constexpr float NOT_FIRED_R = 3.0e38f;
 
 struct RefArgs {
     int n_seeds;
@@ -746,7 +745,7 @@ __global__ void __launch_bounds__(128) refine_kernel(DevGeom G, DevField F, Scan
         a.flags[i] = CDC_FLAG_BAD_HIT;
         return;
     }
-    const float* dtab = a.drift_tab + (size_t)e * G.n_wires;
+    const float* dtab = a.drift_tab + (size_t)e * event_stride(G.n_wires);
     double sd[5];
     float sf[5];
     for (int m = 0; m < 5; ++m) {
@@ -833,33 +832,11 @@ __global__ void __launch_bounds__(128) refine_kernel(DevGeom G, DevField F, Scan
     a.flags[i] = flags;
 }
 
-__global__ void fill_f32_kernel(float* p, long long n, float v) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = v;
-}
-
-__global__ void stage_refine_kernel(int n_events, const int32_t* __restrict__ hit_off,
-                                    const int32_t* __restrict__ wire_id, const float* __restrict__ drift, int n_wires,
-                                    float max_drift, float* drift_tab) {
-    const int total = hit_off[n_events];
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < total; h += gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_events - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (hit_off[mid] <= h) lo = mid; else hi = mid - 1;
-        }
-        int w = wire_id[h];
-        float d = drift[h];
-        if (w < 0 || w >= n_wires || !(d >= 0.f && d <= max_drift)) continue;
-        atomicMin((int*)&drift_tab[(size_t)lo * n_wires + w], __float_as_int(d));
-    }
-}
-
 cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& P, const RefineLaunch& L,
                           float* drift_tab, int num_sms, int do_gn, cudaStream_t st) {
-    fill_f32_kernel<<<num_sms * 4, 256, 0, st>>>(drift_tab, (long long)L.n_events * G.n_wires, NOT_FIRED_R);
-    stage_refine_kernel<<<num_sms * 4, 256, 0, st>>>(L.n_events, L.hit_off, L.wire_id, L.drift, G.n_wires,
-                                                      P.max_drift, drift_tab);
+    cudaError_t err = launch_stage(G, L.n_events, L.hit_off, L.wire_id, L.drift, P.max_drift, drift_tab, nullptr,
+                                   num_sms, st);
+    if (err != cudaSuccess) return err;
     RefArgs a{L.n_seeds, L.seed_event, L.seeds, L.n_events, L.hit_off, drift_tab, L.n_iter, L.sigma,
               {L.scale[0], L.scale[1], L.scale[2], L.scale[3], L.scale[4]}, L.checkpoint, L.seeds_out, L.chi2, L.grad,
               L.n_used, L.flags};

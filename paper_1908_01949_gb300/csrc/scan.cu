@@ -14,11 +14,23 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float NOT_FIRED = 3.0e38f;   // drift-table sentinel (above any valid drift)
 
 // ---------------------------------------------------------------- staging
-// drift_tab[e][wire] = drift of the event's hit on that wire; validates the
-// wire id and drift range; duplicate wires keep the smaller drift and flag.
-__global__ void stage_kernel(int n_events, const int32_t* __restrict__ hit_off, const int32_t* __restrict__ wire_id,
-                             const float* __restrict__ drift, int n_wires, float max_drift, float* drift_tab,
-                             uint32_t* flags) {
+// Event table of event e: tab[e][wire] = drift of the event's hit on that wire
+// and the fired bit of the wire; validates the wire id and drift range;
+// duplicate wires keep the smaller drift and flag.
+__global__ void clear_tables_kernel(float* tab, int n_events, int n_wires) {
+    const int stride = (int)event_stride(n_wires);
+    for (int e = blockIdx.y; e < n_events; e += gridDim.y) {
+        float* t = tab + (size_t)e * stride;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < stride; j += gridDim.x * blockDim.x)
+            t[j] = j < n_wires ? NOT_FIRED : 0.f;  // 0.f: all fired bits clear
+    }
+}
+
+__global__ void stage_kernel(DevGeom G, int n_events, const int32_t* __restrict__ hit_off,
+                             const int32_t* __restrict__ wire_id, const float* __restrict__ drift, float max_drift,
+                             float* tab, uint32_t* flags) {
+    const int n_wires = G.n_wires;
+    const size_t stride = event_stride(n_wires);
     const int total = hit_off[n_events];
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < total; h += gridDim.x * blockDim.x) {
         int lo = 0, hi = n_events - 1;
@@ -29,17 +41,34 @@ __global__ void stage_kernel(int n_events, const int32_t* __restrict__ hit_off, 
         int w = wire_id[h];
         float d = drift[h];
         if (w < 0 || w >= n_wires || !(d >= 0.f && d <= max_drift)) {
-            atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
+            if (flags) atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
             continue;
         }
-        int old = atomicMin((int*)&drift_tab[(size_t)lo * n_wires + w], __float_as_int(d));
-        if (old != __float_as_int(NOT_FIRED)) atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
+        float* t = tab + (size_t)lo * stride;
+        int old = atomicMin((int*)&t[w], __float_as_int(d));
+        if (old != __float_as_int(NOT_FIRED) && flags) atomicOr(&flags[lo], CDC_FLAG_BAD_HIT);
+        int a = 0, b = G.n_layers - 1;  // layer of the wire
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (G.layers[mid].base <= w) a = mid; else b = mid - 1;
+        }
+        const DevLayer& L = G.layers[a];
+        uint32_t* bits = (uint32_t*)(t + n_wires) + L.bword;
+        const int i = w - L.base;
+        atomicOr(bits + (i >> 5), 1u << (i & 31));
+        if (i < 32) atomicOr(bits + ((L.N + i) >> 5), 1u << ((L.N + i) & 31));
     }
 }
 
-__global__ void fill_kernel(float* p, long long n, float v) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = v;
+cudaError_t launch_stage(const DevGeom& G, int n_events, const int32_t* hit_off, const int32_t* wire_id,
+                         const float* drift, float max_drift, float* tab, uint32_t* flags, int num_sms,
+                         cudaStream_t st) {
+    if (n_events <= 0) return cudaSuccess;
+    const int stride = (int)event_stride(G.n_wires);
+    const dim3 cg((stride + 255) / 256, n_events < 65535 ? n_events : 65535);
+    clear_tables_kernel<<<cg, 256, 0, st>>>(tab, n_events, G.n_wires);
+    stage_kernel<<<num_sms * 4, 256, 0, st>>>(G, n_events, hit_off, wire_id, drift, max_drift, tab, flags);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- prologue
@@ -172,7 +201,7 @@ __global__ void __launch_bounds__(256, 3) scan_kernel(DevGeom G, DevField F, Sca
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
                     event_seed(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
-                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * G.n_wires, &s_cand[0][threadIdx.x], 256, sd,
+                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_cand[0][threadIdx.x], 256, sd,
                            FL);
                 } else {
                     my = -2;
@@ -387,7 +416,7 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
     }
     Tracer<KIND> T;
     FoundList FL;
-    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * G.n_wires, &s_cand[0][threadIdx.x], 128, sd, FL);
+    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * event_stride(G.n_wires), &s_cand[0][threadIdx.x], 128, sd, FL);
     while (T.step(G, F, P, s_lay, s_tab, FL))
         if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
     for (int h = h0; h < h1; ++h) {
@@ -540,11 +569,10 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                         const ScanLaunch& L, int num_sms, cudaStream_t st) {
     cudaError_t err;
     const int ne = L.n_events;
-    // stage the event hits into per-event drift tables
-    fill_kernel<<<num_sms * 4, 256, 0, st>>>(W.drift_tab, (long long)ne * G.n_wires, NOT_FIRED);
-    stage_kernel<<<num_sms * 4, 256, 0, st>>>(ne, L.hit_off, L.wire_id, L.drift, G.n_wires, P.max_drift,
-                                               W.drift_tab, L.flags);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // stage the event hits into per-event hit tables
+    if ((err = launch_stage(G, ne, L.hit_off, L.wire_id, L.drift, P.max_drift, W.drift_tab, L.flags, num_sms, st)) !=
+        cudaSuccess)
+        return err;
     int occ = 0;
     if (F.kind == 0)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scan_kernel<0>, 256, 0);

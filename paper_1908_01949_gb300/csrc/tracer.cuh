@@ -15,7 +15,8 @@
 // next rebuild; for tracks nearly parallel to the wires receding wires are kept
 // too.  Approaching wires whose minimum provably lies beyond the list's
 // lifetime (the slope of g is bounded by |t_perp|^2 plus a curvature term)
-// wait for a later list, so lists hold only imminent minima.  Each step then evaluates, for the listed wires only, the derivative of
+// wait for a later list, so lists hold only imminent minima.  Each step then
+// evaluates, for the listed wires only, the derivative of
 // the squared distance to the wire line, g = (r - m)_perp . t, at the new
 // state; a sign change from - to + brackets a local minimum of the distance,
 // which Newton iterations on the cubic Hermite interpolant of the segment
@@ -44,11 +45,13 @@ struct FoundList {
 };
 
 // Visits the fired wires in the search window (half widths band [mm] in
-// radius and d_win [mm] along the layer) around (rho, phi, z): fn(wire, drift, cosa).
+// radius and d_win <= TAB_BAND [mm] along the layer) around (rho, phi, z):
+// fn(wire, drift, cosa).  The layer's fired bits of the window's cells come
+// from one 64-bit read; only fired wires touch the drift table.
 template <class Fn>
 __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2* s_tab, const float* dtab,
-                                             float max_drift, float band, float d_win, float rho, float phi, float z,
-                                             Fn&& fn) {
+                                             const uint32_t* fired, float max_drift, float band, float d_win,
+                                             float rho, float phi, float z, Fn&& fn) {
     const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
     if (lr.x > lr.y) return;
     const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
@@ -64,10 +67,19 @@ __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2
         if (!(fabsf(c) < 1.0e6f)) continue;  // non-finite state: nothing to look up
         const float w = d_win * L.cells_per_mm;
         const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
-        for (int i = i0; i <= i1; ++i) {
-            int ii = i;  // |c| stays near N/2 at most: a few wraps at worst
-            while (ii < 0) ii += L.N;
-            while (ii >= L.N) ii -= L.N;
+        if (i1 < i0) continue;
+        int s0 = i0;  // |c| stays near N/2 at most: a few wraps at worst
+        while (s0 < 0) s0 += L.N;
+        while (s0 >= L.N) s0 -= L.N;
+        const uint32_t* fw = fired + L.bword + (s0 >> 5);
+        const unsigned long long pair = ((unsigned long long)__ldg(fw + 1) << 32) | __ldg(fw);
+        // the geometry keeps i1 - i0 <= 31 (window of at most 32 cells)
+        uint32_t m = (uint32_t)(pair >> (s0 & 31)) & (0xffffffffu >> (31 - min(i1 - i0, 31)));
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            int ii = s0 + b;
+            if (ii >= L.N) ii -= L.N;
             const int wire = L.base + ii;
             const float d = __ldg(dtab + wire);
             if (d <= max_drift) fn(wire, d, L.cosa);
@@ -151,10 +163,32 @@ __device__ __forceinline__ bool in_chamber(const uchar2* s_tab, float rho) {
     return lr.x <= lr.y;
 }
 
+// Squared residual of the distance minimum to wire W inside the segment
+// o -> n (slopes g0 < 0 <= g1, drift d), or +inf where cheap bounds rule out
+// |D - d| < sqrt(lambda) (with 0.01 mm to spare): D <= min(D0, D1), and with
+// D^2' = 2 g and g' >= -kap |w_perp| (kap = |lam| b_max), D^2 >= D0^2 + 2 g0 h
+// - kap (D0 + h) h^2 and D^2 >= D1^2 - 2 g1 h - kap (D1 + h) h^2.
+__device__ __forceinline__ float seg_res2(const ScanConst& P, float kap, float ox, float oy, float oz, float otx,
+                                          float oty, float otz, float nx, float ny, float nz, float ntx, float nty,
+                                          float ntz, float4 W, float cosa, float d, float g0, float g1) {
+    const float h = P.h;
+    const float D0 = point_doca(ox, oy, oz, W, cosa), D1 = point_doca(nx, ny, nz, W, cosa);
+    const float kh2 = kap * h * h;
+    const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, D0 + h, D0 * D0)),
+                            fmaf(-2.0f * h, g1, fmaf(-kh2, D1 + h, D1 * D1)));
+    const float hi = d + P.sqrt_lam + 0.01f, lo = d - P.sqrt_lam - 0.01f;
+    if (lb2 > hi * hi || fminf(D0, D1) < lo) return INFINITY;
+    const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W, cosa,
+                             g0, g1, h) - d;
+    return r * r;
+}
+
 template <int KIND>
 struct Tracer {
     State s;
+    float ox, oy, oz, otx, oty, otz;  // state before the last step (high words)
     const float* dtab;
+    const uint32_t* fired;
     float4* cand;   // this thread's list column: cand[k * stride] = (wire bits, g, drift, cosa)
     int stride;
     int n, part, nf, nc;
@@ -191,10 +225,11 @@ struct Tracer {
         }
     }
 
-    // Candidate list for the next LIST_M segments, built at the current state.
-    __device__ __forceinline__ void rebuild(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
-                                            const uchar2* s_tab) {
-        nc = 0;
+    // Candidates for the next LIST_M segments at the current state:
+    // sink(wire, g, drift, cosa) stores one and returns false when full.
+    template <class Sink>
+    __device__ __forceinline__ void collect(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                           const uchar2* s_tab, Sink&& sink) {
         over = false;
         const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
         const float rho = rho_of(x, y);
@@ -204,36 +239,49 @@ struct Tracer {
         // |t_perp|^2 + w_perp . t' with |t'| <= |lam| b_max = kap, |w_perp| grows
         // by at most 1 per mm and |t_perp|^2 by at most 2 kap per mm, so over an
         // arc s, g rises by at most s (|t_perp|^2 + kap (|w_perp| + 1.5 s)).
+        // Distance bound: along the tangent line the distance to the wire line
+        // never drops below sqrt(|w_perp|^2 - g^2 / |t_perp|^2), and over an arc
+        // s <= reach the track leaves that line by at most kap reach^2 / 2.
         const float reach = wide + 0.5f;
         const float kap = fabsf(s.lam) * P.b_max;
-        visit_window(s_lay, s_tab, dtab, P.max_drift, P.band + wide, P.d_win + wide, rho, atan2f(y, x), z,
+        const float bend = fmaf(0.5f * kap, reach * reach, 0.01f);
+        visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band + wide, P.d_win + wide, rho, atan2f(y, x), z,
                      [&](int wire, float d, float cosa) {
                          const float4 W = __ldg(G.wires + wire);
                          float tp2;
                          const float g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
                          bool keep = tp2 < PARALLEL_T2;
                          if (!keep && g < 0.f) {
-                             // a wire whose minimum provably lies beyond the next LIST_M
-                             // steps waits for a later list
                              const float wp = point_doca(x, y, z, W, cosa);
-                             keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, wp), tp2), g) + 1e-3f >= 0.f;
+                             // the minimum lies within the next LIST_M steps (else a later list
+                             // takes the wire) and can come within d + sqrt(lambda) of the wire
+                             const float dl = sqrtf(fmaxf(fmaf(-g / tp2, g, wp * wp), 0.f));
+                             keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, wp), tp2), g) + 1e-3f >= 0.f &&
+                                    dl - bend <= d + P.sqrt_lam;
                          }
-                         if (keep) {
-                             if (nc < LIST_CAP) {
-                                 cand[nc * stride] = make_float4(__int_as_float(wire), g, d, cosa);
-                                 ++nc;
-                             } else {
-                                 over = true;
-                             }
-                         }
+                         if (keep && !sink(wire, g, d, cosa)) over = true;
                      });
     }
 
+    // Per-lane candidate list in this thread's column.
+    __device__ __forceinline__ void rebuild(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                            const uchar2* s_tab) {
+        nc = 0;
+        collect(G, P, s_lay, s_tab, [&](int wire, float g, float d, float cosa) {
+            if (nc >= LIST_CAP) return false;
+            cand[nc * stride] = make_float4(__int_as_float(wire), g, d, cosa);
+            ++nc;
+            return true;
+        });
+    }
+
+    // Seed state, the start-of-track minima and the first candidate list.
     __device__ __forceinline__ void init(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
                                          const uchar2* s_tab, const float* dtab_, float4* cand_, int stride_,
                                          const float* sd, FoundList& FL) {
         seed_state(sd, G.R0d, P.charge_dir, P.direction, s);
         dtab = dtab_;
+        fired = (const uint32_t*)(dtab_ + G.n_wires);
         cand = cand_;
         stride = stride_;
         n = 0;
@@ -249,7 +297,7 @@ struct Tracer {
         const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
         const float rho = rho_of(x, y);
         if (in_chamber(s_tab, rho))
-            visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(y, x), z,
+            visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(y, x), z,
                          [&](int wire, float d, float cosa) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
@@ -261,53 +309,57 @@ struct Tracer {
         rebuild(G, P, s_lay, s_tab);
     }
 
-    // One RKN step and the minima inside the new segment; false once the track ended.
-    __device__ __forceinline__ bool step(const DevGeom& G, const DevField& F, const ScanConst& P,
-                                         const DevLayer* s_lay, const uchar2* s_tab, FoundList& FL) {
-        const float ox = s.rx, oy = s.ry, oz = s.rz, otx = s.tx, oty = s.ty, otz = s.tz;
+    // One RKN step; the previous state stays in (ox .. otz).
+    __device__ __forceinline__ void advance(const DevField& F, const ScanConst& P) {
+        ox = s.rx;
+        oy = s.ry;
+        oz = s.rz;
+        otx = s.tx;
+        oty = s.ty;
+        otz = s.tz;
         rkn_step<KIND>(F, s, P.h, P.h6_lo);
         ++n;
+    }
+
+    // Minima of this lane's listed wires inside the last segment.
+    __device__ __forceinline__ void list_pass(const DevGeom& G, const ScanConst& P, FoundList& FL) {
+        if (over) return;
+        const float kap = fabsf(s.lam) * P.b_max;
+        for (int k = 0; k < nc; ++k) {
+            float4 e = cand[k * stride];
+            const int wire = __float_as_int(e.x);
+            const float4 W = __ldg(G.wires + wire);
+            float tp2;
+            const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, tp2);
+            if (e.y < 0.f && g1 >= 0.f)
+                found(P, FL, wire, part,
+                      seg_res2(P, kap, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, e.z, e.y,
+                               g1));
+            e.y = g1;
+            cand[k * stride] = e;
+        }
+    }
+
+    // Window search for a lane whose list overflowed, turn bookkeeping, stop
+    // tests and the track-end minima; false once the track ended.
+    __device__ __forceinline__ bool finish(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                           const uchar2* s_tab, FoundList& FL) {
         const float nx = s.rx, ny = s.ry, nz = s.rz, ntx = s.tx, nty = s.ty, ntz = s.tz;
         const float rho = rho_of(nx, ny);
-        const int pt = part;
-        const float h = P.h;
-        const float kap = fabsf(s.lam) * P.b_max;
-        auto seg = [&](int wire, float d, float cosa, float g0, float g1, float4 W) {
-            // Bounds on the distance of closest approach D before the Newton
-            // search: D <= min(D0, D1), and with D^2' = 2 g and g' >= -kap |w_perp|,
-            // D^2 >= D0^2 + 2 g0 h - kap (D0 + h) h^2 and D^2 >= D1^2 - 2 g1 h -
-            // kap (D1 + h) h^2.  A residual |D - d| provably above sqrt(lambda)
-            // (with 0.01 mm to spare) cannot score.
-            const float D0 = point_doca(ox, oy, oz, W, cosa), D1 = point_doca(nx, ny, nz, W, cosa);
-            const float kh2 = kap * h * h;
-            const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, D0 + h, D0 * D0)),
-                                    fmaf(-2.0f * h, g1, fmaf(-kh2, D1 + h, D1 * D1)));
-            const float hi = d + P.sqrt_lam + 0.01f, lo = d - P.sqrt_lam - 0.01f;
-            if (lb2 > hi * hi || fminf(D0, D1) < lo) return;
-            const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W,
-                                     cosa, g0, g1, h) - d;
-            found(P, FL, wire, pt, r * r);
-        };
-        if (!over) {
-            for (int k = 0; k < nc; ++k) {
-                float4 e = cand[k * stride];
-                const int wire = __float_as_int(e.x);
-                const float4 W = __ldg(G.wires + wire);
-                float tp2;
-                const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, e.w, tp2);
-                if (e.y < 0.f && g1 >= 0.f) seg(wire, e.z, e.w, e.y, g1, W);
-                e.y = g1;
-                cand[k * stride] = e;
-            }
-        } else if (in_chamber(s_tab, rho)) {
-            visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
+        if (over && in_chamber(s_tab, rho)) {
+            const int pt = part;
+            const float kap = fabsf(s.lam) * P.b_max;
+            visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
                          [&](int wire, float d, float cosa) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
                              const float g0 = dist_slope(ox, oy, oz, otx, oty, otz, W, cosa, tp2);
                              if (!(g0 < 0.f)) return;
                              const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2);
-                             if (g1 >= 0.f) seg(wire, d, cosa, g0, g1, W);
+                             if (g1 >= 0.f)
+                                 found(P, FL, wire, pt,
+                                       seg_res2(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa,
+                                                d, g0, g1));
                          });
         }
         const bool now_out = rho >= G.R0;
@@ -322,22 +374,31 @@ struct Tracer {
             stop = true;
             flags |= CDC_FLAG_STEP_CAP;
         }
-        if (stop && part < P.max_part) {
-            // end of the track: a minimum if the distance is still shrinking there
+        if (stop && part < P.max_part && in_chamber(s_tab, rho)) {
+            // end of the track: a minimum if the distance is still shrinking
+            // there (the lists hold only imminent minima, so the end looks at
+            // the whole window)
             const int pe = part;
-            auto end_min = [&](int wire, float d, float cosa) {
-                const float4 W = __ldg(G.wires + wire);
-                float tp2;
-                if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
-                    const float r = point_doca(nx, ny, nz, W, cosa) - d;
-                    found(P, FL, wire, pe, r * r);
-                }
-            };
-            // (the list holds only imminent minima, so the end looks at the whole window)
-            if (in_chamber(s_tab, rho))
-                visit_window(s_lay, s_tab, dtab, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz, end_min);
+            visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
+                         [&](int wire, float d, float cosa) {
+                             const float4 W = __ldg(G.wires + wire);
+                             float tp2;
+                             if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
+                                 const float r = point_doca(nx, ny, nz, W, cosa) - d;
+                                 found(P, FL, wire, pe, r * r);
+                             }
+                         });
         }
         return !stop;
+    }
+
+    // One RKN step and the minima inside the new segment (per-lane list);
+    // false once the track ended.
+    __device__ __forceinline__ bool step(const DevGeom& G, const DevField& F, const ScanConst& P,
+                                         const DevLayer* s_lay, const uchar2* s_tab, FoundList& FL) {
+        advance(F, P);
+        list_pass(G, P, FL);
+        return finish(G, P, s_lay, s_tab, FL);
     }
 
     __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
