@@ -361,7 +361,7 @@ def _target_point(rng, z_range=(-400.0, 400.0), r_target=100.0):
     return np.array([r * math.cos(ph), r * math.sin(ph), rng.uniform(*z_range)])
 
 
-def _signal(g, f, rng, turns, max_tries=20000, min_hits=20, p=SIGNAL_P):
+def _signal(g, f, rng, turns, max_tries=20000, min_hits=20, p=SIGNAL_P, max_hits=None):
     """Draw a signal e- from the target that reaches layer >= 4, leaves through
     |z| > z_half between R0 and R_out and makes the requested number of turns."""
     wm, wd, _ = wire_lines(g)
@@ -388,7 +388,7 @@ def _signal(g, f, rng, turns, max_tries=20000, min_hits=20, p=SIGNAL_P):
         if not (abs(pos[-1, 2]) > g.z_half and g.R0 <= rho[-1] <= g.R_out):
             continue
         hits = track_hits(g, wm, wd, pos, lab)
-        if len(hits) < min_hits:
+        if len(hits) < min_hits or (max_hits is not None and len(hits) > max_hits):
             continue
         seeds = np.array([crossing_seed(pos, dirs, i, g.R0, p) for i in cr])
         return hits, seeds, len(cr), r0, p * t
@@ -421,12 +421,12 @@ def _dio_hits(g, f, rng, target_wires, taken, wm, wd):
 
 def make_event(g: Geometry, f: Field, rng: np.random.Generator, turns=(1,),
                noise: str = "uniform", n_noise: int = 40, occupancy: float = 0.0,
-               sigma: float = 0.2, max_drift: float = 8.0) -> Event:
+               sigma: float = 0.2, max_drift: float = 8.0, min_hits: int = 20, max_hits=None) -> Event:
     """One event: a signal e- plus noise.  noise='uniform': n_noise random wires
     with drift U[0, max_drift]; noise='dio': DIO-like tracks up to `occupancy`
     of all wires."""
     wm, wd, _ = wire_lines(g)
-    hits, seeds, nt, r0, p0 = _signal(g, f, rng, turns)
+    hits, seeds, nt, r0, p0 = _signal(g, f, rng, turns, min_hits=min_hits, max_hits=max_hits)
     wires = sorted(hits)
     drift = [min(max(hits[w][0] + rng.normal(0.0, sigma), 0.0), max_drift) for w in wires]
     part = [hits[w][1] for w in wires]
@@ -506,3 +506,45 @@ def cfg2_case(index: int = 0, field_map: Field | None = None, occupancy: float =
     f = field_map if field_map is not None else solenoid_map()
     ev = make_event(g, f, rng, turns=(2, 3), noise="dio", occupancy=occupancy)
     return g, f, ev
+
+
+# ------------------------------------------------------------ batched events
+CFG3_EVENTS = 256
+CFG3_SEEDS = (1.0e4, 1.0e6)
+
+
+def scaled_grid(truth_seed, n_seeds: float, rng: np.random.Generator) -> np.ndarray:
+    """The multi-turn grid with every axis count scaled by f = (n_seeds / 10^6)^(1/5)
+    (steps scaled by the inverse ratio, so each axis keeps its span): (theta0,
+    px0, py0) around the truth plus a random sub-step offset, (z0, pz0) around 0."""
+    tmpl = cfg2_grid_template()
+    n0 = tmpl["n"][0].astype(np.float64)
+    s0 = tmpl["step"][0].astype(np.float64)
+    f = (float(n_seeds) / float(np.prod(n0))) ** 0.2
+    n = np.maximum(1, np.round(n0 * f)).astype(np.int32)
+    step = s0 * n0 / n
+    centre = np.array([truth_seed[0], 0.0, truth_seed[2], truth_seed[3], 0.0])
+    off = rng.uniform(-0.5, 0.5, 5) * step
+    off[[1, 4]] = 0.0
+    return make_grid(centre + off, step, n)
+
+
+def cfg3_event(index: int, field_map: Field | None = None, seeds=CFG3_SEEDS):
+    """One event of the batched workload: a signal e- of 1-3 turns with 30-200
+    hits, DIO-like noise at an occupancy uniform in 5-20 %, and a seed grid whose
+    size is log-uniform in `seeds` (the multi-turn grid scaled, see scaled_grid)."""
+    rng = np.random.default_rng(BASE_SEED + 2000 + index)
+    g = make_geometry()
+    f = field_map if field_map is not None else solenoid_map()
+    occ = rng.uniform(0.05, 0.20)
+    n_seeds = math.exp(rng.uniform(math.log(seeds[0]), math.log(seeds[1])))
+    ev = make_event(g, f, rng, turns=(1, 2, 3), noise="dio", occupancy=occ, min_hits=30, max_hits=200)
+    return ev, scaled_grid(ev.truth_seeds[0], n_seeds, rng)
+
+
+def cfg3_case(n_events: int = CFG3_EVENTS, field_map: Field | None = None, seeds=CFG3_SEEDS, first: int = 0):
+    """Batched workload: geometry, field, events and grids [n_events]."""
+    f = field_map if field_map is not None else solenoid_map()
+    out = [cfg3_event(first + i, f, seeds) for i in range(n_events)]
+    grids = np.concatenate([gr for _, gr in out])
+    return make_geometry(), f, [ev for ev, _ in out], grids

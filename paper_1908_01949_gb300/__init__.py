@@ -15,7 +15,7 @@ from ._lib import (CAND_DTYPE, CDC_MAX_K, CDC_MAX_ZOOM, EXPORTS, FLAG_BAD_HIT, F
                    FLAG_FOUND_OVERFLOW, FLAG_LOST_HIT, FLAG_NOT_SPD, FLAG_STEP_CAP, GRID_BYTES, GRID_DTYPE, CdcError,
                    Context, grids_to_tensor, hough_params, lib, refine_params, scan_params, tensor_to_grids)
 
-__all__ = ["Context", "Tracker", "CdcError", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
+__all__ = ["Context", "Tracker", "CdcError", "chi2", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
            "tensor_to_grids", "GRID_DTYPE", "CAND_DTYPE", "EXPORTS", "lib"]
 
 
@@ -115,6 +115,42 @@ class Tracker:
         self.ctx.cdc_chi2_grad(n, seed_event, seeds, int(hit_off.numel()) - 1, hit_off, wire_id, drift, scan, params,
                                out["chi2"], out["grad"], out["n_used"], out["flags"], stream)
         return out
+
+
+_CHI2_FN = None
+
+
+def _chi2_function():
+    """torch.autograd.Function: chi^2 of the assigned hits' DOCA residuals of
+    each seed (forward) and d chi^2 / d seed from the adjoint RKN kernel
+    (backward), both from one cdc_chi2_grad call."""
+    global _CHI2_FN
+    if _CHI2_FN is None:
+        import torch
+
+        class Chi2(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, seeds, tracker, seed_event, hit_off, wire_id, drift, scan, params):
+                out = tracker.chi2_grad(seed_event, seeds.detach().contiguous(), hit_off, wire_id, drift, scan,
+                                        params, want_grad=True)
+                ctx.save_for_backward(out["grad"])
+                ctx.extra = (out["n_used"], out["flags"])
+                return out["chi2"]
+
+            @staticmethod
+            def backward(ctx, g):
+                (grad,) = ctx.saved_tensors
+                return (g.to(grad.dtype)[:, None] * grad,) + (None,) * 7
+
+        _CHI2_FN = Chi2
+    return _CHI2_FN
+
+
+def chi2(tracker, seed_event, seeds, hit_off, wire_id, drift, scan, params):
+    """Differentiable chi^2 [n_seeds] (float64) of seeds [n_seeds, 5] (float32,
+    may require grad); the hit assignment of each seed is taken at the seed
+    itself, as in cdc_chi2_grad."""
+    return _chi2_function().apply(seeds, tracker, seed_event, hit_off, wire_id, drift, scan, params)
 
 
 def decode_candidates(t):

@@ -110,3 +110,25 @@ def test_seed_event_out_of_range_is_flagged():
     fl = out["flags"].cpu().numpy()
     assert fl[1] & cdc.FLAG_BAD_HIT and np.isnan(out["chi2"][1].item())
     assert not (fl[0] & cdc.FLAG_BAD_HIT)
+
+
+def test_autograd_function_backward_is_the_adjoint_gradient():
+    """cdc.chi2 as a torch.autograd.Function: backward of sum(w * chi2) gives
+    w_i * d chi2_i / d seed_i, the adjoint gradient of cdc_chi2_grad."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, seeds, mp, ms = _cases("uniform")
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    sp = cdc.scan_params(h=2.0, max_steps=ms, lam=4.0, max_partitions=mp)
+    rp = cdc.refine_params(n_iter=0, sigma=0.2, checkpoint=128)
+    se = torch.zeros(len(seeds), dtype=torch.int32, device=tr.dev)
+    x = torch.as_tensor(seeds, device=tr.dev).clone().requires_grad_(True)
+    c = cdc.chi2(tr, se, x, off, wid, dr, sp, rp)
+    w = torch.arange(1, len(seeds) + 1, dtype=torch.float64, device=tr.dev)
+    (w * c).sum().backward()
+    ref = tr.chi2_grad(se, torch.as_tensor(seeds, device=tr.dev), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    assert torch.equal(c.detach(), ref["chi2"])
+    expect = (w.float()[:, None] * ref["grad"]).cpu().numpy()
+    assert np.allclose(x.grad.cpu().numpy(), expect, rtol=1e-6, atol=0)
