@@ -19,6 +19,12 @@ Batched leg (timed separately): 256 events with 1-3 turn signals of 30-200
 hits, 5-20 % DIO-like occupancy and log-uniform 10^4-10^6 seeds per event,
 all ten rounds of all events in one CUDA-graph replay per step.
 
+Sweep leg (timed separately): 64 events at 30 % occupancy with 10^7 seeds in
+one CUDA graph; the batched Hough of all 64 events; and the FP32 scan and
+refine steppers against the FP64 GPU stepper at every 0.5 m up to 6 m on a
+10^4-seed subsample (the FP64 GPU stepper itself is tested against the FP64
+oracle).
+
 --profile-case shrinks the coarse grid to 240000 seeds (6 pz0 values) for
 profiler captures; its line is marked as such and is not a benchmark result.
 
@@ -160,13 +166,49 @@ def _gen_cfg3(i):
     return S.cfg3_event(i, _GEN_FIELD)
 
 
-def make_batched_workload(n_events, first=0):
-    """The batched events, generated by a spawn pool (host only)."""
+def _gen_cfg5(i):
+    import cdc_synth as S
+    return S.cfg5_event(i, _GEN_FIELD)
+
+
+def make_batched_workload(n_events, first=0, gen=_gen_cfg3):
+    """Events generated by a spawn pool (host only)."""
     import multiprocessing as mp
     import cdc_synth as S
     with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 32), initializer=_gen_init) as pool:
-        out = pool.map(_gen_cfg3, range(first, first + n_events), chunksize=1)
+        out = pool.map(gen, range(first, first + n_events), chunksize=1)
     return [ev for ev, _ in out], np.concatenate([gr for _, gr in out]), S
+
+
+def graph_scan(tr, off_t, wid_t, dr_t, gr_t, sp, warmup):
+    """The whole scan call (all rounds, all events) captured in one CUDA graph."""
+    import torch
+    side = torch.cuda.Stream(device=tr.dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
+    side.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        out = tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
+    for _ in range(max(warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    return graph, out
+
+
+def time_graph(graph, out, flush, reps):
+    import torch
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times), int(out["steps"].sum())
 
 
 def batched_leg(args, rank, local, g, fm, flush):
@@ -185,28 +227,8 @@ def batched_leg(args, rank, local, g, fm, flush):
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
     off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
     gr_t = cdc.grids_to_tensor(grids, tr.dev)
-    side = torch.cuda.Stream(device=tr.dev)
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
-    side.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=side):
-        out = tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
-    for _ in range(max(args.warmup, 3)):
-        graph.replay()
-    torch.cuda.synchronize()
-    times, steps = [], 0
-    for _ in range(args.batched_steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        graph.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        steps = int(out["steps"].sum())
-    ms = statistics.median(times)
+    graph, out = graph_scan(tr, off_t, wid_t, dr_t, gr_t, sp, args.warmup)
+    ms, steps = time_graph(graph, out, flush, args.batched_steps)
     seeds_step = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
     fl = out["flags"].cpu().numpy()
     return {"events": n_ev, "coarse_seeds": n, "seeds_per_step": seeds_step,
@@ -215,6 +237,86 @@ def batched_leg(args, rank, local, g, fm, flush):
             "events_per_s": n_ev / (ms / 1e3), "graph": "one CUDA graph per step (all rounds, all events)",
             "flagged_events": int((fl != 0).sum()), "timing": f"median of {args.batched_steps} graph replays, "
                                                               "L2 flushed before each"}
+
+
+SWEEP_EVERY, SWEEP_REC, SWEEP_SEEDS = 250, 12, 10_000
+
+
+def sweep_leg(args, rank, local, g, fm, flush):
+    """Precision/scale sweep: scan throughput at 30 % occupancy (10^7 seeds
+    over 64 events, one CUDA graph), the batched Hough of all events, and the
+    position difference of the FP32 steppers from the FP64 GPU stepper against
+    path length (0.5-6 m) on a 10^4-seed subsample of the events' grids."""
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    n_ev = int(args.sweep_events)
+    evs, grids, _ = make_batched_workload(n_ev, first=1000 * rank, gen=_gen_cfg5)
+    counts = [int(np.prod(gr["n"])) for gr in grids]
+    n = sum(counts)
+    off, wid, dr = S.pack_events(evs)
+    tr = cdc.Tracker(g, fm, device=local, max_events=n_ev, max_seeds=n, max_hits=int(wid.size))
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
+                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    gr_t = cdc.grids_to_tensor(grids, tr.dev)
+    graph, out = graph_scan(tr, off_t, wid_t, dr_t, gr_t, sp, args.warmup)
+    ms, steps = time_graph(graph, out, flush, args.batched_steps)
+    seeds_step = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
+    # batched Hough of all events
+    hp = cdc.hough_params(grid_template=S.cfg2_grid_template())
+    h = tr.hough(off_t, wid_t, hp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    h = tr.hough(off_t, wid_t, hp)
+    e1.record()
+    torch.cuda.synchronize()
+    hough_ms = e0.elapsed_time(e1)
+    votes = int(h["acc"].sum(dtype=torch.int64))
+    # FP32 steppers against the FP64 GPU stepper
+    rng = np.random.default_rng(3)
+    pick = np.sort(rng.choice(n, size=min(SWEEP_SEEDS, n), replace=False))
+    base = np.concatenate([[0], np.cumsum(counts)])
+    ev_of = np.searchsorted(base, pick, side="right") - 1
+    seeds = np.stack([grid_value(grids[e], int(i - base[e])) for e, i in zip(ev_of, pick)]).astype(np.float32)
+    gs = S.sweep_geometry(g)
+    ts = cdc.Tracker(gs, fm, device=local, max_events=1, max_seeds=1, max_hits=1)
+    pp = cdc.scan_params(h=H, max_steps=SWEEP_EVERY * SWEEP_REC, lam=LAM, max_partitions=16)
+    ds = torch.as_tensor(seeds, device=ts.dev)
+    pos = {prec: ts.propagate(ds, pp, every=SWEEP_EVERY, n_rec=SWEEP_REC, precision=prec)["pos"].cpu().numpy()
+           for prec in (0, 2, 1)}
+    curve = []
+    for r in range(SWEEP_REC):
+        path_m = SWEEP_EVERY * (r + 1) * H / 1000.0
+        row = {"path_m": path_m}
+        for prec, name in ((0, "scan_fp32"), (2, "refine_fp32")):
+            d = np.linalg.norm(pos[prec][:, r] - pos[1][:, r], axis=1)
+            d = d[np.isfinite(d)]
+            row[name] = {"max_mm": float(d.max()) if d.size else None,
+                         "median_mm": float(np.median(d)) if d.size else None,
+                         "max_mm_per_m": float(d.max() / path_m) if d.size else None, "seeds": int(d.size)}
+        curve.append(row)
+    return {"events": n_ev, "occupancy": 0.30, "coarse_seeds": n, "seeds_per_step": seeds_step,
+            "hits": int(wid.size), "ms_per_step": ms, "seeds_per_s": seeds_step / (ms / 1e3),
+            "rkn_steps_per_s": steps / (ms / 1e3),
+            "hough": {"events": n_ev, "ms": hough_ms, "votes": votes,
+                      "votes_per_s": votes / (hough_ms / 1e3)},
+            "position_vs_fp64_gpu": curve,
+            "subsample": f"{seeds.shape[0]} seeds drawn from the events' grids, fixed-length propagation "
+                         f"(no stop surfaces) to {SWEEP_EVERY * SWEEP_REC * H / 1000.0:.0f} m"}
+
+
+def grid_value(gr, i):
+    """Seed i (row-major) of one grid record, each value c + k s rounded once to FP32."""
+    n = [int(x) for x in gr["n"]]
+    k = []
+    for a in range(4, -1, -1):
+        k.append(i % n[a])
+        i //= n[a]
+    k = k[::-1]
+    return np.array([np.float32(float(gr["centre"][a]) + (k[a] - (n[a] - 1) / 2.0) * float(gr["step"][a]))
+                     for a in range(5)])
 
 
 REFINE_K, REFINE_SLOTS, REFINE_ITER, REFINE_CKPT, REFINE_SIGMA = 64, 1024, 5, 128, 0.2
@@ -396,6 +498,9 @@ def run_cuda(args, ws, rank, local):
     batched = None
     if not args.no_batched and not args.profile_case:
         batched = batched_leg(args, rank, local, g, fm, flush)
+    sweep = None
+    if not args.no_sweep and not args.profile_case:
+        sweep = sweep_leg(args, rank, local, g, fm, flush)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
@@ -416,6 +521,7 @@ def run_cuda(args, ws, rank, local):
         "refine_seeds_per_s": refine["seeds_per_s"] if refine else None,
         "refine": refine,
         "batched": batched,
+        "sweep": sweep,
         "events_per_s": {"scan": ws / (ms / 1e3),
                          "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
@@ -522,6 +628,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 256-event leg")
     ap.add_argument("--batched-events", type=int, default=256, help="events of the batched leg")
     ap.add_argument("--batched-steps", type=int, default=3, help="timed graph replays of the batched leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 30 %%-occupancy precision/scale leg")
+    ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
     args = ap.parse_args()

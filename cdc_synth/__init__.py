@@ -548,3 +548,23 @@ def cfg3_case(n_events: int = CFG3_EVENTS, field_map: Field | None = None, seeds
     out = [cfg3_event(first + i, f, seeds) for i in range(n_events)]
     grids = np.concatenate([gr for _, gr in out])
     return make_geometry(), f, [ev for ev, _ in out], grids
+
+
+CFG5_EVENTS = 64
+CFG5_SEEDS = 1.0e7
+
+
+def cfg5_event(index: int, field_map: Field | None = None, n_seeds: float = CFG5_SEEDS / CFG5_EVENTS):
+    """One event of the precision/scale sweep: a 1-3 turn signal and DIO-like
+    noise at 30 % occupancy, with a scaled multi-turn grid of ~n_seeds seeds."""
+    rng = np.random.default_rng(BASE_SEED + 3000 + index)
+    g = make_geometry()
+    f = field_map if field_map is not None else solenoid_map()
+    ev = make_event(g, f, rng, turns=(1, 2, 3), noise="dio", occupancy=0.30)
+    return ev, scaled_grid(ev.truth_seeds[0], n_seeds, rng)
+
+
+def sweep_geometry(g: Geometry) -> Geometry:
+    """The chamber without its stop surfaces (|z| and rho limits far outside), for
+    fixed-length propagation of the precision sweep."""
+    return Geometry(R=g.R, alpha=g.alpha, N=g.N, phi_off=g.phi_off, z_half=5000.0, R0=g.R0, R_out=980.0)
