@@ -54,6 +54,7 @@ WORKLOAD = ("single multi-turn 104.97 MeV e- event, solenoid map 451x1001 @ 2 mm
             "10 scan rounds (coarse + 9 zoom x 4 x 3^5); RKN h=2 mm, <=3500 steps, 3 partitions; "
             "hit classification of the best seed")
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
+SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune_scan's timings
 H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
 
 
@@ -124,6 +125,12 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream):
+    """The step's seed grid (Hough output), computed once before tuning."""
+    ctx.cdc_hough_seeds(ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream)
+    return grid
 
 
 def reduce_max(value: float, dist=None, device=None) -> float:
@@ -227,6 +234,8 @@ def batched_leg(args, rank, local, g, fm, flush):
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
     off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
     gr_t = cdc.grids_to_tensor(grids, tr.dev)
+    n_tune = min(n_ev, 32)    # tune on the first 32 events (one coarse round per shape)
+    tuned, tune_ms = tr.tune(off_t[:n_tune + 1], wid_t, dr_t, gr_t[:n_tune], sp, reps=1)
     graph, out = graph_scan(tr, off_t, wid_t, dr_t, gr_t, sp, args.warmup)
     ms, steps = time_graph(graph, out, flush, args.batched_steps)
     seeds_step = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
@@ -235,6 +244,8 @@ def batched_leg(args, rank, local, g, fm, flush):
             "coarse_seeds_min_max": [min(counts), max(counts)], "hits": int(wid.size), "ms_per_step": ms,
             "seeds_per_s": seeds_step / (ms / 1e3), "rkn_steps_per_s": steps / (ms / 1e3),
             "events_per_s": n_ev / (ms / 1e3), "graph": "one CUDA graph per step (all rounds, all events)",
+            "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]}, "ms_by_shape": tune_ms,
+                         "events": n_tune},
             "flagged_events": int((fl != 0).sum()), "timing": f"median of {args.batched_steps} graph replays, "
                                                               "L2 flushed before each"}
 
@@ -426,6 +437,8 @@ def run_cuda(args, ws, rank, local):
         ctx.cdc_scan_seeds(ne, o, w, d, grid, sp, None, topk0, best_E, best_seed, hit_part, None, None, sflags,
                            steps, stream)
 
+    tuned, tune_ms = tr.tune(off, wid, dr, grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags,
+                                                            stream), sp, reps=3, stream=stream)
     launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan fill+stage, 5/round, 9 zoom grids, assign
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     for _ in range(args.warmup):
@@ -518,6 +531,8 @@ def run_cuda(args, ws, rank, local):
         "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
         "coarse_scan": {"launch_ms": statistics.mean(coarse_ms) if coarse_ms else None, "rkn_steps": coarse_steps,
                         "seeds": seeds_coarse},
+        "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]},
+                     "shapes": [{"block": b, "chunk": c} for b, c in SCAN_SHAPES], "coarse_round_ms": tune_ms},
         "refine_seeds_per_s": refine["seeds_per_s"] if refine else None,
         "refine": refine,
         "batched": batched,

@@ -254,6 +254,40 @@ int cdc_propagate(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_
 int cdc_kernel_timer(cdc_ctx* ctx, int enable);
 int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* per_launch_ms, int cap);
 
+/* ---- launch shape of the seed scan and its autotuner -------------------- */
+
+/* Launch shape of the seed-scan kernel (no counterpart in the paper, which
+ * launches one block per seed, sec. 3): block = threads, i.e. seeds in
+ * flight, per block (128 or 256); chunk = RKN steps a lane takes between
+ * seed refills (16 or 32).  Every shape keeps 768 resident threads per SM and
+ * computes bit-identical results; the shape changes only the speed.  A new
+ * context uses {256, 16}. */
+typedef struct {
+    int32_t block;
+    int32_t chunk;
+} cdc_scan_config;
+
+#define CDC_SCAN_CONFIGS 4 /* shapes tried by cdc_tune_scan, in this order: */
+/* {256, 16}, {256, 32}, {128, 16}, {128, 32} */
+
+/* Set / read the shape used by later cdc_scan_seeds calls on ctx.  Errors:
+ * CDC_ERR_ARG (NULL), CDC_ERR_RANGE (block not 128/256 or chunk not 16/32). */
+int cdc_set_scan_config(cdc_ctx* ctx, const cdc_scan_config* cfg);
+int cdc_get_scan_config(const cdc_ctx* ctx, cdc_scan_config* cfg);
+
+/* Autotuner: runs the coarse round of the given events (arguments as in
+ * cdc_scan_seeds, device pointers; params->n_rounds is taken as 1) once as a
+ * warm-up and `reps` (1..20) more times under each of the CDC_SCAN_CONFIGS
+ * shapes, keeps the shape with the lowest median time for later scans on ctx,
+ * and returns it in best (host, nullable) and each shape's median time [ms]
+ * in ms (host, CDC_SCAN_CONFIGS entries, nullable).  Synchronous setup call:
+ * it allocates and frees temporary device buffers and waits for the GPU, so it
+ * must not run during stream capture.  Errors as cdc_scan_seeds, plus
+ * CDC_ERR_NOMEM. */
+int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id, const float* drift,
+                  const cdc_grid* grids, const cdc_scan_params* params, int reps, cdc_scan_config* best, float* ms,
+                  void* stream);
+
 /* ---- allocation-free scan ---------------------------------------------- */
 
 #define CDC_NOALLOC_MAX_EVENTS 8

@@ -83,6 +83,12 @@ class Tracker:
                                 out["steps"], stream)
         return out
 
+    def tune(self, hit_off, wire_id, drift, grids, params, reps=3, stream=None):
+        """Autotune the scan kernel's launch shape on these events (synchronous);
+        later scans on this tracker use the fastest shape."""
+        ne = int(hit_off.numel()) - 1
+        return self.ctx.cdc_tune_scan(ne, hit_off, wire_id, drift, grids, params, reps, stream)
+
     def propagate(self, seeds, params, every, n_rec, precision=0, stream=None):
         t = self.torch
         n = int(seeds.shape[0])

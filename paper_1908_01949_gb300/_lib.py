@@ -34,7 +34,8 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 # All entry points of include/cdc.h.
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
-           "cdc_kernel_timer", "cdc_kernel_time", "cdc_scan_seeds_noalloc"]
+           "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
+           "cdc_scan_seeds_noalloc"]
 
 
 class cdc_grid(C.Structure):
@@ -62,6 +63,13 @@ class cdc_candidate(C.Structure):
 class cdc_refine_params(C.Structure):
     _fields_ = [("n_iter", C.c_int32), ("sigma", C.c_float), ("scale", C.c_float * 5), ("checkpoint", C.c_int32)]
 
+
+class cdc_scan_config(C.Structure):
+    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32)]
+
+
+CDC_SCAN_CONFIGS = 4
+SCAN_CONFIGS = [(256, 16), (256, 32), (128, 16), (128, 32)]   # the order cdc_tune_scan times them in
 
 GRID_BYTES = C.sizeof(cdc_grid)            # 60
 CAND_BYTES = C.sizeof(cdc_candidate)       # 28
@@ -104,6 +112,10 @@ def lib():
         L.cdc_scan_seeds_noalloc.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp, vp, vp,
                                              vp, vp, vp, vp]
         L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
+        L.cdc_set_scan_config.argtypes = [vp, P(cdc_scan_config)]
+        L.cdc_get_scan_config.argtypes = [vp, P(cdc_scan_config)]
+        L.cdc_tune_scan.argtypes = [vp, C.c_int, vp, vp, vp, vp, P(cdc_scan_params), C.c_int, P(cdc_scan_config),
+                                    vp, vp]
         for name in EXPORTS:
             if name not in ("cdc_destroy", "cdc_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -294,6 +306,27 @@ class Context:
             _dev(best_seed, torch.float32, "best_seed", d), _dev(hit_part, torch.int8, "hit_part", d, True),
             _dev(hit_res2, torch.float32, "hit_res2", d, True), _dev(flags, torch.int32, "flags", d),
             _dev(steps, torch.int64, "steps", d, True), _stream(stream)))
+
+    def cdc_set_scan_config(self, block, chunk):
+        return self._check(self.L.cdc_set_scan_config(self.h, C.byref(cdc_scan_config(int(block), int(chunk)))))
+
+    def cdc_get_scan_config(self):
+        cfg = cdc_scan_config()
+        self._check(self.L.cdc_get_scan_config(self.h, C.byref(cfg)))
+        return cfg.block, cfg.chunk
+
+    def cdc_tune_scan(self, n_events, hit_off, wire_id, drift, grids, params, reps=3, stream=None):
+        """Times the coarse round under every launch shape and keeps the fastest:
+        ((block, chunk), [median ms per shape in SCAN_CONFIGS order])."""
+        import torch
+        d = self.device
+        best = cdc_scan_config()
+        ms = np.zeros(CDC_SCAN_CONFIGS, np.float32)
+        self._check(self.L.cdc_tune_scan(
+            self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(wire_id, torch.int32, "wire_id", d),
+            _dev(drift, torch.float32, "drift", d), _dev(grids, torch.uint8, "grids", d), C.byref(params), int(reps),
+            C.byref(best), ms.ctypes.data, _stream(stream)))
+        return (best.block, best.chunk), [float(x) for x in ms]
 
     def cdc_kernel_timer(self, enable):
         return self._check(self.L.cdc_kernel_timer(self.h, int(bool(enable))))

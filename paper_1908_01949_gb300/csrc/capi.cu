@@ -40,6 +40,8 @@ struct cdc_ctx {
     int2* d_offsets = nullptr;
     size_t offsets_cap = 0;
     int off_key[4] = {-1, -1, -1, -1};
+    // scan-kernel launch shape (cdc_scan_config)
+    int scan_block = 256, scan_chunk = 16;
     // kernel timer
     bool timer_on = false;
     std::vector<cudaEvent_t> timer_ev;
@@ -430,8 +432,95 @@ int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32
     ScanLaunch L{n_events, hit_off, wire_id, drift, grids, E, topk0, best_E, best_seed, hit_part, hit_res2, zoom_grids,
                  flags, steps, p->n_rounds, p->n_rounds > 1 ? p->n_zoom : 1, KernelTimer{}};
     if (c->timer_on) L.timer = KernelTimer{c->timer_ev.data(), (int)c->timer_ev.size(), &c->timer_used};
+    L.block = c->scan_block;
+    L.chunk = c->scan_chunk;
     e = launch_scan(c->G, c->F, make_const(c, p), c->W, L, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scan launch");
+    return CDC_OK;
+}
+
+static const cdc_scan_config SCAN_CONFIGS[CDC_SCAN_CONFIGS] = {{256, 16}, {256, 32}, {128, 16}, {128, 32}};
+
+int cdc_set_scan_config(cdc_ctx* c, const cdc_scan_config* cfg) {
+    if (!c || !cfg) return c ? fail(c, CDC_ERR_ARG, "NULL config") : CDC_ERR_ARG;
+    if ((cfg->block != 128 && cfg->block != 256) || (cfg->chunk != 16 && cfg->chunk != 32))
+        return fail(c, CDC_ERR_RANGE, "scan config: block must be 128 or 256, chunk 16 or 32");
+    c->scan_block = cfg->block;
+    c->scan_chunk = cfg->chunk;
+    return CDC_OK;
+}
+
+int cdc_get_scan_config(const cdc_ctx* c, cdc_scan_config* cfg) {
+    if (!c || !cfg) return CDC_ERR_ARG;
+    cfg->block = c->scan_block;
+    cfg->chunk = c->scan_chunk;
+    return CDC_OK;
+}
+
+int cdc_tune_scan(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32_t* wire_id, const float* drift,
+                  const cdc_grid* grids, const cdc_scan_params* p, int reps, cdc_scan_config* best, float* ms,
+                  void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (!p) return fail(c, CDC_ERR_ARG, "scan params is NULL");
+    if (n_events < 1) return fail(c, CDC_ERR_ARG, "n_events must be >= 1");
+    if (reps < 1 || reps > 20) return fail(c, CDC_ERR_RANGE, "reps outside 1..20");
+    cdc_scan_params p1 = *p;
+    p1.n_rounds = 1;
+    int rc = check_scan_params(c, &p1, true);
+    if (rc) return rc;
+    if (!hit_off || !wire_id || !drift || !grids) return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (n_events > c->W.max_events || c->W.n_wires < c->G.n_wires)
+        return fail(c, CDC_ERR_NOT_LOADED, "workspace too small: call cdc_reserve");
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    float *bE = nullptr, *bS = nullptr;
+    uint32_t* fl = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(bE, (size_t)n_events * p1.k)) != cudaSuccess ||
+        (e = dalloc(bS, (size_t)n_events * p1.k * 5)) != cudaSuccess || (e = dalloc(fl, (size_t)n_events)) != cudaSuccess) {
+        dfree(bE);
+        dfree(bS);
+        dfree(fl);
+        return fail(c, CDC_ERR_NOMEM, std::string("tuner buffers: ") + cudaGetErrorString(e));
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const ScanConst P = make_const(c, &p1);
+    float med[CDC_SCAN_CONFIGS];
+    int bi = 0;
+    for (int i = 0; i < CDC_SCAN_CONFIGS && e == cudaSuccess; ++i) {
+        ScanLaunch L{n_events, hit_off, wire_id, drift, grids, nullptr, nullptr, bE, bS, nullptr, nullptr, nullptr,
+                     fl, nullptr, 1, 1, KernelTimer{}};
+        L.block = SCAN_CONFIGS[i].block;
+        L.chunk = SCAN_CONFIGS[i].chunk;
+        std::vector<float> t;
+        for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, st);
+            e = launch_scan(c->G, c->F, P, c->W, L, c->num_sms, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float x = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+            if (r > 0) t.push_back(x);  // the first run warms up
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t.begin(), t.end());
+        med[i] = t[t.size() / 2];
+        if (med[i] < med[bi]) bi = i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(bE);
+    dfree(bS);
+    dfree(fl);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning run");
+    c->scan_block = SCAN_CONFIGS[bi].block;
+    c->scan_chunk = SCAN_CONFIGS[bi].chunk;
+    if (best) *best = SCAN_CONFIGS[bi];
+    if (ms)
+        for (int i = 0; i < CDC_SCAN_CONFIGS; ++i) ms[i] = med[i];
     return CDC_OK;
 }
 
@@ -546,7 +635,7 @@ namespace cdc {
 // Context view for the allocation-free scan (noalloc.cu): validates the scan
 // parameters exactly as cdc_scan_seeds does and hands out the loaded tables.
 int scan_view(cdc_ctx* c, const cdc_scan_params* p, DevGeom* G, DevField* F, ScanConst* P, int* num_sms,
-              int* device) {
+              int* device, int* block, int* chunk) {
     if (!c) return CDC_ERR_ARG;
     if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
     int rc = check_scan_params(c, p, true);
@@ -556,6 +645,8 @@ int scan_view(cdc_ctx* c, const cdc_scan_params* p, DevGeom* G, DevField* F, Sca
     *P = make_const(c, p);
     *num_sms = c->num_sms;
     *device = c->device;
+    *block = c->scan_block;
+    *chunk = c->scan_chunk;
     return CDC_OK;
 }
 

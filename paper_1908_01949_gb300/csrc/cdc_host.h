@@ -47,6 +47,7 @@ struct ScanLaunch {
     unsigned long long* steps;
     int n_rounds, n_zoom;
     KernelTimer timer;
+    int block = 256, chunk = 16;  // scan-kernel launch shape (cdc_scan_config)
 };
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.

@@ -20,7 +20,7 @@
 
 namespace cdc {
 int scan_view(cdc_ctx* c, const cdc_scan_params* p, DevGeom* G, DevField* F, ScanConst* P, int* num_sms,
-              int* device);
+              int* device, int* block, int* chunk);
 int set_error(cdc_ctx* c, int code, const char* msg);
 }  // namespace cdc
 
@@ -100,8 +100,8 @@ extern "C" int cdc_scan_seeds_noalloc(cdc_ctx* c, int n_events, int64_t n_seeds,
     DevGeom G;
     DevField F;
     ScanConst P;
-    int sms = 1, dev = 0;
-    int rc = scan_view(c, p, &G, &F, &P, &sms, &dev);
+    int sms = 1, dev = 0, block = 256, chunk = 16;
+    int rc = scan_view(c, p, &G, &F, &P, &sms, &dev, &block, &chunk);
     if (rc) return rc;
     if (n_events == 0) return CDC_OK;
     if (!hit_off || !wire_id || !drift || !grids || !best_E || !best_seed || !flags)
@@ -131,6 +131,8 @@ extern "C" int cdc_scan_seeds_noalloc(cdc_ctx* c, int n_events, int64_t n_seeds,
     if (e != cudaSuccess) return set_error(c, CDC_ERR_CUDA, "flags reset failed");
     ScanLaunch L{n_events, hit_off, wire_id, drift, grids, E, topk0, best_E, best_seed, hit_part, hit_res2, nullptr,
                  flags, steps, 1, 1, KernelTimer{}};
+    L.block = block;
+    L.chunk = chunk;
     e = launch_scan(G, F, P, W, L, sms, st);
     if (e != cudaSuccess) return set_error(c, CDC_ERR_CUDA, cudaGetErrorString(e));
     return CDC_OK;

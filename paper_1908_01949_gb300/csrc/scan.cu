@@ -169,14 +169,17 @@ struct ScanIO {
 };
 
 // Persistent thread-per-seed scorer.  Each lane takes seeds from a global
-// counter (warp-aggregated atomics) and steps its seed in chunks of 16 RKN
+// counter (warp-aggregated atomics) and steps its seed in chunks of CHUNK RKN
 // steps; a lane whose seed ended takes a new one at the next chunk boundary,
 // so lanes stay busy although seeds end after very different step counts.
-template <int KIND>
-__global__ void __launch_bounds__(256, 3) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+// BS threads per block, 768 resident threads per SM for every shape (the
+// register budget stays 80 per thread).
+template <int KIND, int BS, int CHUNK>
+__global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+    static_assert(CHUNK % LIST_M == 0, "candidate lists restart at chunk boundaries");
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
-    __shared__ float4 s_cand[LIST_CAP][256];
+    __shared__ float4 s_cand[LIST_CAP][BS];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
@@ -201,8 +204,8 @@ __global__ void __launch_bounds__(256, 3) scan_kernel(DevGeom G, DevField F, Sca
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
                     event_seed(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
-                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_cand[0][threadIdx.x], 256, sd,
-                           FL);
+                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires),
+                           &s_cand[0][threadIdx.x], BS, sd, FL);
                 } else {
                     my = -2;
                 }
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(256, 3) scan_kernel(DevGeom G, DevField F, Sca
         }
         if (__all_sync(FULL, my == -2)) break;
         if (my >= 0) {
-            for (int it = 0; it < 16; ++it) {
+            for (int it = 0; it < CHUNK; ++it) {
                 if (!T.step(G, F, P, s_lay, s_tab, FL)) {
                     int H = io.hit_off[ev + 1] - io.hit_off[ev];
                     io.E[my] = T.score(P, H);
@@ -565,6 +568,14 @@ __global__ void propagate_fp64_kernel(DevGeom G, DevField F, ScanConst P, int n_
 // ----------------------------------------------------------- launchers
 static int blocks_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
+using ScanKernel = void (*)(DevGeom, DevField, ScanConst, ScanIO);
+
+template <int KIND>
+static ScanKernel scan_kernel_of(int block, int chunk) {
+    if (block == 128) return chunk == 32 ? scan_kernel<KIND, 128, 32> : scan_kernel<KIND, 128, 16>;
+    return chunk == 32 ? scan_kernel<KIND, 256, 32> : scan_kernel<KIND, 256, 16>;
+}
+
 cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
                         const ScanLaunch& L, int num_sms, cudaStream_t st) {
     cudaError_t err;
@@ -573,11 +584,10 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
     if ((err = launch_stage(G, ne, L.hit_off, L.wire_id, L.drift, P.max_drift, W.drift_tab, L.flags, num_sms, st)) !=
         cudaSuccess)
         return err;
+    const int bs = L.block == 128 ? 128 : 256;
+    const ScanKernel kern = F.kind == 0 ? scan_kernel_of<0>(bs, L.chunk) : scan_kernel_of<1>(bs, L.chunk);
     int occ = 0;
-    if (F.kind == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scan_kernel<0>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scan_kernel<1>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0);
     const int scan_blocks = num_sms * (occ > 0 ? occ : 1);
     for (int r = 0; r < L.n_rounds; ++r) {
         const cdc_grid* grids = r == 0 ? L.grids0 : W.zgrids + (size_t)(r & 1) * W.max_events * CDC_MAX_ZOOM;
@@ -604,10 +614,7 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                   L.steps ? L.steps + r : nullptr};
         const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
         if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
-        if (F.kind == 0)
-            scan_kernel<0><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
-        else
-            scan_kernel<1><<<scan_blocks, 256, 0, st>>>(G, F, P, io);
+        kern<<<scan_blocks, bs, 0, st>>>(G, F, P, io);
         if (timed) {
             cudaEventRecord(L.timer.ev[*L.timer.used + 1], st);
             *L.timer.used += 2;

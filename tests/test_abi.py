@@ -55,14 +55,16 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.cdc_candidate) == 28
     assert C.sizeof(_lib.cdc_hough_params) == 13 * 4 + 60
     assert C.sizeof(_lib.cdc_refine_params) == 32
+    assert C.sizeof(_lib.cdc_scan_config) == 8
     # compile a probe against the header and compare sizes/offsets
     probe = r'''
 #include <stdio.h>
 #include <stddef.h>
 #include "cdc.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cdc_grid), sizeof(cdc_scan_params),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(cdc_grid), sizeof(cdc_scan_params),
  sizeof(cdc_candidate), sizeof(cdc_hough_params), sizeof(cdc_refine_params),
- offsetof(cdc_hough_params, grid_template), offsetof(cdc_scan_params, max_drift)); return 0;}
+ offsetof(cdc_hough_params, grid_template), offsetof(cdc_scan_params, max_drift), sizeof(cdc_scan_config),
+ CDC_SCAN_CONFIGS); return 0;}
 '''
     import tempfile
     with tempfile.TemporaryDirectory() as d:
@@ -73,7 +75,8 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cdc_grid), sizeof(
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     assert vals == [C.sizeof(_lib.cdc_grid), C.sizeof(_lib.cdc_scan_params), C.sizeof(_lib.cdc_candidate),
                     C.sizeof(_lib.cdc_hough_params), C.sizeof(_lib.cdc_refine_params),
-                    _lib.cdc_hough_params.grid_template.offset, _lib.cdc_scan_params.max_drift.offset]
+                    _lib.cdc_hough_params.grid_template.offset, _lib.cdc_scan_params.max_drift.offset,
+                    C.sizeof(_lib.cdc_scan_config), _lib.CDC_SCAN_CONFIGS]
 
 
 def test_null_context_is_an_argument_error(libcdc):
@@ -85,6 +88,9 @@ def test_null_context_is_an_argument_error(libcdc):
     L.cdc_scan_seeds.restype = C.c_int
     assert L.cdc_scan_seeds(*([None] * 17)) == -1
     assert L.cdc_load_geometry(None, 0, None, None, None, None, C.c_double(0), C.c_double(0), C.c_double(0)) == -1
+    assert L.cdc_set_scan_config(None, None) == -1
+    assert L.cdc_get_scan_config(None, None) == -1
+    assert L.cdc_tune_scan(*([None] * 11)) == -1
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -85,3 +85,35 @@ def test_graph_replay_equals_eager(field_map):
         a, b = eager[key], out[key]
         assert torch.equal(a, b), key
     assert torch.equal(eager["steps"], out["steps"])
+
+
+def test_every_launch_shape_is_bit_identical_and_the_tuner_keeps_one(field_map):
+    """The scan kernel's launch shapes (threads per block, steps between seed
+    refills) change no result bit; cdc_tune_scan times them all and keeps
+    the fastest for later scans."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    from paper_1908_01949_gb300._lib import SCAN_CONFIGS
+    g, f, evs, grids = _case(field_map)
+    n = sum(int(np.prod(gr["n"])) for gr in grids)
+    tr = tracker(g, f, max_events=N_EVENTS, max_seeds=n)
+    p = cdc.scan_params(h=2.0, max_steps=3500, lam=4.0, max_partitions=3, k=8, n_rounds=3, n_zoom=4, max_drift=8.0)
+    ref = None
+    for block, chunk in SCAN_CONFIGS:
+        tr.ctx.cdc_set_scan_config(block, chunk)
+        assert tr.ctx.cdc_get_scan_config() == (block, chunk)
+        out, _ = _run(tr, evs, grids, p, n)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = out
+            continue
+        for key in ("E", "topk0", "best_E", "best_seed", "hit_part", "hit_res2", "flags", "steps"):
+            assert torch.equal(ref[key], out[key]), (block, chunk, key)
+    off, wid, dr = S.pack_events(evs)
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    best, ms = tr.tune(off_t, wid_t, dr_t, cdc.grids_to_tensor(grids, tr.dev), p, reps=2)
+    assert best in SCAN_CONFIGS and len(ms) == len(SCAN_CONFIGS) and min(ms) > 0
+    assert ms[SCAN_CONFIGS.index(best)] == min(ms)
+    assert tr.ctx.cdc_get_scan_config() == best
+    with pytest.raises(cdc.CdcError):
+        tr.ctx.cdc_set_scan_config(64, 16)
