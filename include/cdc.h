@@ -256,29 +256,35 @@ int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* pe
 
 /* ---- launch shape of the seed scan and its autotuner -------------------- */
 
-/* Launch shape of the seed-scan kernel (no counterpart in the paper, which
- * launches one block per seed, sec. 3): block = threads, i.e. seeds in
- * flight, per block (128 or 256); chunk = RKN steps a lane takes between
- * seed refills (16 or 32).  Every shape keeps 768 resident threads per SM and
- * computes bit-identical results; the shape changes only the speed.  A new
- * context uses {256, 16}. */
+/* Launch shape of the seed scan (no counterpart in the paper, which launches
+ * one block per seed, sec. 3).  block = threads, i.e. seeds in flight, per
+ * block of the one-lane-per-seed kernel (128 or 256); chunk = RKN steps a lane
+ * takes between seed refills (16 or 32); warp_seeds = zoom rounds with at most
+ * this many seeds (n_events * n_zoom * 243) run one warp per seed instead,
+ * which shortens rounds too small to fill the GPU (0: never).  Every shape
+ * keeps 768 resident threads per SM; the results do not depend on block and
+ * chunk, and the warp kernel records the same minima in the same order.  A
+ * new context uses {256, 16, 16 * number of SMs}. */
 typedef struct {
     int32_t block;
     int32_t chunk;
+    int32_t warp_seeds;
 } cdc_scan_config;
 
 #define CDC_SCAN_CONFIGS 4 /* shapes tried by cdc_tune_scan, in this order: */
 /* {256, 16}, {256, 32}, {128, 16}, {128, 32} */
 
 /* Set / read the shape used by later cdc_scan_seeds calls on ctx.  Errors:
- * CDC_ERR_ARG (NULL), CDC_ERR_RANGE (block not 128/256 or chunk not 16/32). */
+ * CDC_ERR_ARG (NULL), CDC_ERR_RANGE (block not 128/256, chunk not 16/32 or
+ * warp_seeds < 0). */
 int cdc_set_scan_config(cdc_ctx* ctx, const cdc_scan_config* cfg);
 int cdc_get_scan_config(const cdc_ctx* ctx, cdc_scan_config* cfg);
 
 /* Autotuner: runs the coarse round of the given events (arguments as in
  * cdc_scan_seeds, device pointers; params->n_rounds is taken as 1) once as a
  * warm-up and `reps` (1..20) more times under each of the CDC_SCAN_CONFIGS
- * shapes, keeps the shape with the lowest median time for later scans on ctx,
+ * (block, chunk) shapes, keeps the one with the lowest median time for later
+ * scans on ctx (warp_seeds is left as set),
  * and returns it in best (host, nullable) and each shape's median time [ms]
  * in ms (host, CDC_SCAN_CONFIGS entries, nullable).  Synchronous setup call:
  * it allocates and frees temporary device buffers and waits for the GPU, so it

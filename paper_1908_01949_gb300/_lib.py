@@ -65,7 +65,7 @@ class cdc_refine_params(C.Structure):
 
 
 class cdc_scan_config(C.Structure):
-    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32), ("warp_seeds", C.c_int32)]
 
 
 CDC_SCAN_CONFIGS = 4
@@ -307,13 +307,18 @@ class Context:
             _dev(hit_res2, torch.float32, "hit_res2", d, True), _dev(flags, torch.int32, "flags", d),
             _dev(steps, torch.int64, "steps", d, True), _stream(stream)))
 
-    def cdc_set_scan_config(self, block, chunk):
-        return self._check(self.L.cdc_set_scan_config(self.h, C.byref(cdc_scan_config(int(block), int(chunk)))))
+    def cdc_set_scan_config(self, block, chunk, warp_seeds=None):
+        """Launch shape of later scans; warp_seeds None keeps the current value."""
+        if warp_seeds is None:
+            warp_seeds = self.cdc_get_scan_config()[2]
+        return self._check(self.L.cdc_set_scan_config(
+            self.h, C.byref(cdc_scan_config(int(block), int(chunk), int(warp_seeds)))))
 
     def cdc_get_scan_config(self):
+        """(block, chunk, warp_seeds) of later scans."""
         cfg = cdc_scan_config()
         self._check(self.L.cdc_get_scan_config(self.h, C.byref(cfg)))
-        return cfg.block, cfg.chunk
+        return cfg.block, cfg.chunk, cfg.warp_seeds
 
     def cdc_tune_scan(self, n_events, hit_off, wire_id, drift, grids, params, reps=3, stream=None):
         """Times the coarse round under every launch shape and keeps the fastest:

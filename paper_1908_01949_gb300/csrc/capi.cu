@@ -41,7 +41,7 @@ struct cdc_ctx {
     size_t offsets_cap = 0;
     int off_key[4] = {-1, -1, -1, -1};
     // scan-kernel launch shape (cdc_scan_config)
-    int scan_block = 256, scan_chunk = 16;
+    int scan_block = 256, scan_chunk = 16, scan_warp_seeds = 0;
     // kernel timer
     bool timer_on = false;
     std::vector<cudaEvent_t> timer_ev;
@@ -161,6 +161,7 @@ int cdc_create(cdc_ctx** out, int device) {
         delete c;
         return CDC_ERR_CUDA;
     }
+    c->scan_warp_seeds = 16 * c->num_sms;
     *out = c;
     return CDC_OK;
 }
@@ -434,19 +435,21 @@ int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32
     if (c->timer_on) L.timer = KernelTimer{c->timer_ev.data(), (int)c->timer_ev.size(), &c->timer_used};
     L.block = c->scan_block;
     L.chunk = c->scan_chunk;
+    L.warp_seeds = c->scan_warp_seeds;
     e = launch_scan(c->G, c->F, make_const(c, p), c->W, L, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scan launch");
     return CDC_OK;
 }
 
-static const cdc_scan_config SCAN_CONFIGS[CDC_SCAN_CONFIGS] = {{256, 16}, {256, 32}, {128, 16}, {128, 32}};
+static const cdc_scan_config SCAN_CONFIGS[CDC_SCAN_CONFIGS] = {{256, 16, 0}, {256, 32, 0}, {128, 16, 0}, {128, 32, 0}};
 
 int cdc_set_scan_config(cdc_ctx* c, const cdc_scan_config* cfg) {
     if (!c || !cfg) return c ? fail(c, CDC_ERR_ARG, "NULL config") : CDC_ERR_ARG;
-    if ((cfg->block != 128 && cfg->block != 256) || (cfg->chunk != 16 && cfg->chunk != 32))
-        return fail(c, CDC_ERR_RANGE, "scan config: block must be 128 or 256, chunk 16 or 32");
+    if ((cfg->block != 128 && cfg->block != 256) || (cfg->chunk != 16 && cfg->chunk != 32) || cfg->warp_seeds < 0)
+        return fail(c, CDC_ERR_RANGE, "scan config: block must be 128 or 256, chunk 16 or 32, warp_seeds >= 0");
     c->scan_block = cfg->block;
     c->scan_chunk = cfg->chunk;
+    c->scan_warp_seeds = cfg->warp_seeds;
     return CDC_OK;
 }
 
@@ -454,6 +457,7 @@ int cdc_get_scan_config(const cdc_ctx* c, cdc_scan_config* cfg) {
     if (!c || !cfg) return CDC_ERR_ARG;
     cfg->block = c->scan_block;
     cfg->chunk = c->scan_chunk;
+    cfg->warp_seeds = c->scan_warp_seeds;
     return CDC_OK;
 }
 
@@ -518,7 +522,10 @@ int cdc_tune_scan(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32_
     if (e != cudaSuccess) return cuda_fail(c, e, "tuning run");
     c->scan_block = SCAN_CONFIGS[bi].block;
     c->scan_chunk = SCAN_CONFIGS[bi].chunk;
-    if (best) *best = SCAN_CONFIGS[bi];
+    if (best) {
+        *best = SCAN_CONFIGS[bi];
+        best->warp_seeds = c->scan_warp_seeds;
+    }
     if (ms)
         for (int i = 0; i < CDC_SCAN_CONFIGS; ++i) ms[i] = med[i];
     return CDC_OK;

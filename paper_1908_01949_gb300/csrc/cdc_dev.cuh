@@ -73,6 +73,34 @@ struct ScanConst {
 };
 
 // ------------------------------------------------------------------ field
+// Map cell holding (x, y, z) (clamped to the grid), the in-cell coordinates
+// (u, v) and 1/rho.
+__device__ __forceinline__ int field_cell(const DevField& F, float x, float y, float z, float& u, float& v,
+                                          float& rinv) {
+    const float r2 = fmaf(x, x, y * y);
+    rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float rho = r2 * rinv;
+    const float rc = fminf(fmaxf(rho, F.r_min), F.r_max);
+    const float zc = fminf(fmaxf(z, F.z_min), F.z_max);
+    u = (rc - F.r_min) * F.inv_dr;
+    v = (zc - F.z_min) * F.inv_dz;
+    const int i = min((int)u, F.nr - 2);
+    const int j = min((int)v, F.nz - 2);
+    u -= (float)i;
+    v -= (float)j;
+    return i * (F.nz - 1) + j;
+}
+
+// Bilinear (Bz, Br) of one cell at (u, v), then Bx = Br x / rho, By = Br y / rho.
+__device__ __forceinline__ void field_apply(float4 cz, float4 cr, float u, float v, float rinv, float x, float y,
+                                            float& bx, float& by, float& bz) {
+    bz = fmaf(v, fmaf(cz.w, u, cz.z), fmaf(cz.y, u, cz.x));
+    const float br = fmaf(v, fmaf(cr.w, u, cr.z), fmaf(cr.y, u, cr.x));
+    const float s = br * rinv;
+    bx = s * x;
+    by = s * y;
+}
+
 template <int KIND>
 __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, float z, float& bx, float& by,
                                            float& bz) {
@@ -81,25 +109,9 @@ __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, 
         by = 0.f;
         bz = F.B0;
     } else {
-        float r2 = fmaf(x, x, y * y);
-        float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        float rho = r2 * rinv;
-        float rc = fminf(fmaxf(rho, F.r_min), F.r_max);
-        float zc = fminf(fmaxf(z, F.z_min), F.z_max);
-        float u = (rc - F.r_min) * F.inv_dr;
-        float v = (zc - F.z_min) * F.inv_dz;
-        int i = min((int)u, F.nr - 2);
-        int j = min((int)v, F.nz - 2);
-        u -= (float)i;
-        v -= (float)j;
-        const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
-        float4 cz = __ldg(c);
-        float4 cr = __ldg(c + 1);
-        bz = fmaf(v, fmaf(cz.w, u, cz.z), fmaf(cz.y, u, cz.x));
-        float br = fmaf(v, fmaf(cr.w, u, cr.z), fmaf(cr.y, u, cr.x));
-        float s = br * rinv;
-        bx = s * x;
-        by = s * y;
+        float u, v, rinv;
+        const float4* c = F.cells + 2 * field_cell(F, x, y, z, u, v, rinv);
+        field_apply(__ldg(c), __ldg(c + 1), u, v, rinv, x, y, bx, by, bz);
     }
 }
 
@@ -262,6 +274,23 @@ __device__ __forceinline__ void grid_seed(const cdc_grid& g, long long idx, floa
     }
 #pragma unroll
     for (int a = 0; a < 5; ++a) out[a] = fmaf((float)ia[a] - 0.5f * (float)(g.n[a] - 1), g.step[a], g.centre[a]);
+}
+
+// Row-major index of the q-th seed of a grid in scan order: (z0, pz0)
+// outermost, then theta0, px0, py0, so that consecutive seeds (the lanes of a
+// warp) differ by a step of a transverse parameter, follow nearly the same
+// path and visit nearly the same wires.
+__device__ __forceinline__ long long scan_order_index(const cdc_grid& g, long long q) {
+    const int nt = g.n[0], nz = g.n[1], nx = g.n[2], ny = g.n[3], np = g.n[4];
+    const long long iy = q % ny;
+    q /= ny;
+    const long long ix = q % nx;
+    q /= nx;
+    const long long it = q % nt;
+    q /= nt;
+    const long long ip = q % np;
+    const long long iz = q / np;
+    return (((it * nz + iz) * nx + ix) * ny + iy) * np + ip;
 }
 
 __device__ __forceinline__ long long grid_count(const cdc_grid& g) {

@@ -48,6 +48,7 @@ struct ScanLaunch {
     int n_rounds, n_zoom;
     KernelTimer timer;
     int block = 256, chunk = 16;  // scan-kernel launch shape (cdc_scan_config)
+    long long warp_seeds = 0;     // zoom rounds of at most this many seeds run one warp per seed
 };
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.

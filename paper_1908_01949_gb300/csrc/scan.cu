@@ -2,11 +2,14 @@
 // persistent thread-per-seed RKN scorer, warp-level top-K, the zoom re-scan
 // grids and the hit-to-turn classification of the best seed.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "cdc_dev.cuh"
 #include "cdc_host.h"
 #include "tracer.cuh"
+#include "warp_tracer.cuh"
 
 namespace cdc {
 
@@ -142,6 +145,25 @@ __device__ __forceinline__ int find_event(const long long* off, int n, long long
     return lo;
 }
 
+// The q-th seed of event e in scan order (scan_order_index within each of the
+// event's grids): its values, and its row-major index among the event's seeds.
+__device__ __forceinline__ long long event_seed_ordered(const cdc_grid* grids, int gpe, int e, long long q,
+                                                       float* sd) {
+    long long base = 0;
+    for (int g = 0; g < gpe; ++g) {
+        const cdc_grid& gr = grids[(size_t)e * gpe + g];
+        const long long c = grid_count(gr);
+        if (q < c || g == gpe - 1) {
+            const long long li = scan_order_index(gr, q);
+            grid_seed(gr, li, sd);
+            return base + li;
+        }
+        q -= c;
+        base += c;
+    }
+    return base;
+}
+
 __device__ __forceinline__ void event_seed(const cdc_grid* grids, int gpe, int e, long long local, float* sd) {
     for (int g = 0; g < gpe; ++g) {
         const cdc_grid& gr = grids[(size_t)e * gpe + g];
@@ -168,10 +190,12 @@ struct ScanIO {
     unsigned long long* steps;
 };
 
-// Persistent thread-per-seed scorer.  Each lane takes seeds from a global
-// counter (warp-aggregated atomics) and steps its seed in chunks of CHUNK RKN
-// steps; a lane whose seed ended takes a new one at the next chunk boundary,
-// so lanes stay busy although seeds end after very different step counts.
+// Persistent thread-per-seed scorer.  A warp takes 32 consecutive seeds in
+// scan order (neighbours in theta0, px0, py0 at equal z0, pz0: nearly the same
+// path, so the lanes search nearly the same wires and stay converged) from a
+// global counter, steps them in chunks of CHUNK RKN steps, and takes the next
+// 32 once all its lanes have ended.  Scores are written at the seeds' row-major
+// indices.
 // BS threads per block, 768 resident threads per SM for every shape (the
 // register budget stays 80 per thread).
 template <int KIND, int BS, int CHUNK>
@@ -192,6 +216,7 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
     unsigned long long nsteps = 0;
     for (;;) {
         unsigned need = __ballot_sync(FULL, my == -1);
+        if ((need | __ballot_sync(FULL, my == -2)) != FULL) need = 0;  // refill whole cohorts only
         if (need) {
             int leader = __ffs(need) - 1;
             unsigned long long base = 0;
@@ -200,10 +225,9 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
             if (my == -1) {
                 long long s = (long long)base + __popc(need & ((1u << lane) - 1u));
                 if (s < total) {
-                    my = s;
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
-                    event_seed(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
+                    my = io.seed_off[ev] + event_seed_ordered(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
                     T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires),
                            &s_cand[0][threadIdx.x], BS, sd, FL);
                 } else {
@@ -386,8 +410,44 @@ __global__ void record_round0_kernel(int n_events, int n_zoom, const cdc_grid* g
     record[(size_t)e * n_zoom + c] = g;
 }
 
+// Warp-per-seed scorer for rounds with few seeds (the zoom rounds of a few
+// events): each warp takes one seed at a time from the global counter and its
+// 32 lanes follow it together (warp_tracer.cuh), which shortens the round,
+// bounded by its longest track, without changing any score.
+template <int KIND>
+__global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+    __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
+    __shared__ uchar2 s_tab[TAB_N];
+    __shared__ WarpFound s_rec[4];
+    for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
+    for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
+    __syncthreads();
+    const long long total = (long long)io.counters[1];
+    const int lane = threadIdx.x & 31;
+    WarpTracer<KIND> T;
+    unsigned long long nsteps = 0;
+    for (;;) {
+        unsigned long long s = 0;
+        if (lane == 0) s = atomicAdd(&io.counters[0], 1ull);
+        s = __shfl_sync(FULL, s, 0);
+        if ((long long)s >= total) break;
+        const int ev = find_event(io.seed_off, io.n_events, (long long)s);
+        float sd[5];
+        event_seed(io.grids, io.gpe, ev, (long long)s - io.seed_off[ev], sd);
+        T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_rec[threadIdx.x >> 5], sd);
+        T.run(G, F, P, s_lay, s_tab);
+        if (lane == 0) {
+            io.E[s] = T.score(P, io.hit_off[ev + 1] - io.hit_off[ev]);
+            if (T.flags) atomicOr(&io.flags[ev], T.flags);
+            nsteps += (unsigned long long)T.n;
+        }
+    }
+    if (io.steps && lane == 0 && nsteps) atomicAdd(io.steps, nsteps);
+}
+
 // Hit classification of each event's best seed (sec. 2.2: hits with
-// d^2 < lambda belong to the partition under investigation).
+// d^2 < lambda belong to the partition under investigation): one warp per
+// event follows the seed (warp_tracer.cuh), then the lanes classify the hits.
 template <int KIND>
 __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, ScanConst P, int n_events,
                                                      const float* __restrict__ drift_tab,
@@ -397,11 +457,11 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
                                                      float* hit_res2) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
-    __shared__ float4 s_cand[LIST_CAP][128];
+    __shared__ WarpFound s_rec[4];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (e >= n_events) return;
     float sd[5];
     bool valid = true;
@@ -411,22 +471,25 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
     }
     const int h0 = hit_off[e], h1 = hit_off[e + 1];
     if (!valid) {
-        for (int h = h0; h < h1; ++h) {
+        for (int h = h0 + lane; h < h1; h += 32) {
             if (hit_part) hit_part[h] = -1;
             if (hit_res2) hit_res2[h] = P.lam;
         }
         return;
     }
-    Tracer<KIND> T;
-    FoundList FL;
-    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * event_stride(G.n_wires), &s_cand[0][threadIdx.x], 128, sd, FL);
-    while (T.step(G, F, P, s_lay, s_tab, FL))
-        if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
-    for (int h = h0; h < h1; ++h) {
-        int w = wire_id[h];
+    WarpFound* rec = &s_rec[threadIdx.x >> 5];
+    WarpTracer<KIND> T;
+    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * event_stride(G.n_wires), rec, sd);
+    T.run(G, F, P, s_lay, s_tab);
+    for (int h = h0 + lane; h < h1; h += 32) {
+        const int w = wire_id[h];
         int part = -1;
         float r2 = P.lam;
-        found_lookup(FL, T.nf, w, part, r2);
+        for (int i = 0; i < T.nf; ++i)
+            if ((int)(rec->key[i] & 0xffffu) == w) {
+                part = (int)(rec->key[i] >> 16);
+                r2 = rec->r2[i];
+            }
         if (hit_part) hit_part[h] = (int8_t)part;
         if (hit_res2) hit_res2[h] = r2;
     }
@@ -614,7 +677,17 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                   L.steps ? L.steps + r : nullptr};
         const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
         if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
-        kern<<<scan_blocks, bs, 0, st>>>(G, F, P, io);
+        // a round of few seeds (host bound: zoom grids of 3^5 seeds) runs one warp per seed
+        const long long round_seeds = (long long)ne * L.n_zoom * ZOOM_GRID;
+        if (r > 0 && round_seeds <= L.warp_seeds) {
+            const int nb = (int)std::min<long long>((round_seeds + 3) / 4, (long long)num_sms * 16);
+            if (F.kind == 0)
+                scan_warp_kernel<0><<<nb, 128, 0, st>>>(G, F, P, io);
+            else
+                scan_warp_kernel<1><<<nb, 128, 0, st>>>(G, F, P, io);
+        } else {
+            kern<<<scan_blocks, bs, 0, st>>>(G, F, P, io);
+        }
         if (timed) {
             cudaEventRecord(L.timer.ev[*L.timer.used + 1], st);
             *L.timer.used += 2;
@@ -628,11 +701,11 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
     }
     if (L.hit_part || L.hit_res2) {
         if (F.kind == 0)
-            assign_kernel<0><<<blocks_for(ne, 128), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
-                                                                  L.best_seed, P.k, L.hit_part, L.hit_res2);
+            assign_kernel<0><<<blocks_for(ne, 4), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
+                                                                L.best_seed, P.k, L.hit_part, L.hit_res2);
         else
-            assign_kernel<1><<<blocks_for(ne, 128), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
-                                                                  L.best_seed, P.k, L.hit_part, L.hit_res2);
+            assign_kernel<1><<<blocks_for(ne, 4), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
+                                                                L.best_seed, P.k, L.hit_part, L.hit_res2);
     }
     return cudaGetLastError();
 }

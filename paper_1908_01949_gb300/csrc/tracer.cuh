@@ -153,6 +153,22 @@ __device__ __forceinline__ float point_doca(float rx, float ry, float rz, float4
     return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
 }
 
+// Squared distance from point r to the wire line.
+__device__ __forceinline__ float point_doca2(float rx, float ry, float rz, float4 W, float cosa) {
+    const float ax = rx - W.x, ay = ry - W.y;
+    const float ad = fmaf(ax, W.z, fmaf(ay, W.w, rz * cosa));
+    const float px = ax - ad * W.z, py = ay - ad * W.w, pz = rz - ad * cosa;
+    return fmaf(px, px, fmaf(py, py, pz * pz));
+}
+
+// An upper bound of sqrt(x), x >= 0, for the conservative filters (the
+// reciprocal square root is good to a few ulp; 1e-5 relative covers it).
+__device__ __forceinline__ float sqrt_ub(float x) {
+    if (!(x > 0.f)) return 0.f;
+    const float s = x * rsqrtf(x);
+    return fmaf(s, 1.0e-5f, s);
+}
+
 __device__ __forceinline__ float rho_of(float x, float y) {
     const float r2 = fmaf(x, x, y * y);
     return r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
@@ -172,12 +188,12 @@ __device__ __forceinline__ float seg_res2(const ScanConst& P, float kap, float o
                                           float oty, float otz, float nx, float ny, float nz, float ntx, float nty,
                                           float ntz, float4 W, float cosa, float d, float g0, float g1) {
     const float h = P.h;
-    const float D0 = point_doca(ox, oy, oz, W, cosa), D1 = point_doca(nx, ny, nz, W, cosa);
+    const float D0s = point_doca2(ox, oy, oz, W, cosa), D1s = point_doca2(nx, ny, nz, W, cosa);
     const float kh2 = kap * h * h;
-    const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, D0 + h, D0 * D0)),
-                            fmaf(-2.0f * h, g1, fmaf(-kh2, D1 + h, D1 * D1)));
+    const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, sqrt_ub(D0s) + h, D0s)),
+                            fmaf(-2.0f * h, g1, fmaf(-kh2, sqrt_ub(D1s) + h, D1s)));
     const float hi = d + P.sqrt_lam + 0.01f, lo = d - P.sqrt_lam - 0.01f;
-    if (lb2 > hi * hi || fminf(D0, D1) < lo) return INFINITY;
+    if (lb2 > hi * hi || (lo > 0.f && fminf(D0s, D1s) < lo * lo)) return INFINITY;
     const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W, cosa,
                              g0, g1, h) - d;
     return r * r;
@@ -252,12 +268,13 @@ struct Tracer {
                          const float g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
                          bool keep = tp2 < PARALLEL_T2;
                          if (!keep && g < 0.f) {
-                             const float wp = point_doca(x, y, z, W, cosa);
                              // the minimum lies within the next LIST_M steps (else a later list
-                             // takes the wire) and can come within d + sqrt(lambda) of the wire
-                             const float dl = sqrtf(fmaxf(fmaf(-g / tp2, g, wp * wp), 0.f));
-                             keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, wp), tp2), g) + 1e-3f >= 0.f &&
-                                    dl - bend <= d + P.sqrt_lam;
+                             // takes the wire) and can come within d + sqrt(lambda) of the wire:
+                             // |w_perp|^2 - g^2 / |t_perp|^2 <= (d + sqrt(lambda) + bend)^2
+                             const float wp2 = point_doca2(x, y, z, W, cosa);
+                             const float lim = d + P.sqrt_lam + bend;
+                             keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, sqrt_ub(wp2)), tp2), g) + 1e-3f >= 0.f &&
+                                    fmaf(wp2, tp2, -g * g) <= lim * lim * tp2;
                          }
                          if (keep && !sink(wire, g, d, cosa)) over = true;
                      });
@@ -403,13 +420,5 @@ struct Tracer {
 
     __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
 };
-
-__device__ __forceinline__ void found_lookup(const FoundList& FL, int nf, int wire, int& pt, float& r2) {
-    for (int i = 0; i < nf; ++i)
-        if ((int)(FL.key[i] & 0xffffu) == wire) {
-            pt = (int)(FL.key[i] >> 16);
-            r2 = FL.r2[i];
-        }
-}
 
 }  // namespace cdc

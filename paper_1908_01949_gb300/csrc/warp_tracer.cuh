@@ -1,0 +1,347 @@
+// Warp-per-seed tracer of the scan (arXiv:1908.01949 sec. 2.2, Eq. 1) for
+// rounds with few seeds.  With one lane per seed such a round leaves the GPU
+// nearly empty and lasts as long as its longest track, so here the 32 lanes of
+// a warp follow one seed together:
+//   - every lane steps the same state with the same arithmetic as Tracer, so
+//     the RKN chain runs without divergence;
+//   - the candidate list holds one wire per lane and its sign tests run in
+//     parallel;
+//   - a window search hands one fired wire to each lane (layer by layer, cell
+//     by cell, the visiting order of visit_window);
+//   - the record of wires scored below lambda lives in shared memory, where
+//     all lanes search it at once.
+// Minima are recorded in the same order as by Tracer, so both compute the
+// same Eq. 1 sums.
+#pragma once
+
+#include "tracer.cuh"
+
+namespace cdc {
+
+constexpr unsigned WARP_ALL = 0xffffffffu;
+constexpr int WARP_LIST_CAP = 32;  // candidate wires per seed: one per lane
+
+// Record of one warp's seed: wire | partition << 16, and res^2.
+struct WarpFound {
+    uint32_t key[CDC_MAX_FOUND];
+    float r2[CDC_MAX_FOUND];
+};
+
+// Fired wire number j of the search window around (rho, phi, z), counted in
+// the visiting order of visit_window, as (wire, cosa), or wire = -1.  Returns
+// the number of fired wires in the window.  All arguments but j are the same
+// on every lane, so the layer loop does not diverge.
+__device__ __forceinline__ int window_nth(const DevLayer* s_lay, const uchar2* s_tab, const uint32_t* fired,
+                                          float band, float d_win, float rho, float phi, float z, int j, int& wire,
+                                          float& cosa) {
+    wire = -1;
+    cosa = 1.f;
+    const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
+    if (lr.x > lr.y) return 0;
+    const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
+    const float blo2 = blo * blo, bhi2 = bhi * bhi, z2 = z * z;
+    int total = 0;
+    for (int l = lr.x; l <= lr.y; ++l) {
+        const DevLayer& L = s_lay[l];
+        const float rl2 = fmaf(z2, L.tan2a, L.R2);
+        if (rl2 > bhi2 || rl2 < blo2) continue;
+        const float zt = z * L.tana_over_R, zt2 = zt * zt;
+        const float tw = zt * fmaf(zt2, fmaf(zt2, fmaf(zt2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
+        const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
+        if (!(fabsf(c) < 1.0e6f)) continue;
+        const float w = d_win * L.cells_per_mm;
+        const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
+        if (i1 < i0) continue;
+        int s0 = i0;
+        while (s0 < 0) s0 += L.N;
+        while (s0 >= L.N) s0 -= L.N;
+        const uint32_t* fw = fired + L.bword + (s0 >> 5);
+        const unsigned long long pair = ((unsigned long long)__ldg(fw + 1) << 32) | __ldg(fw);
+        const uint32_t m = (uint32_t)(pair >> (s0 & 31)) & (0xffffffffu >> (31 - min(i1 - i0, 31)));
+        const int cnt = __popc(m);
+        if (j >= total && j < total + cnt) {
+            int ii = s0 + (int)__fns(m, 0, j - total + 1);
+            if (ii >= L.N) ii -= L.N;
+            wire = L.base + ii;
+            cosa = L.cosa;
+        }
+        total += cnt;
+    }
+    return total;
+}
+
+template <int KIND>
+struct WarpTracer {
+    State s;
+    float ox, oy, oz, otx, oty, otz;  // state before the last step (high words)
+    const float* dtab;
+    const uint32_t* fired;
+    WarpFound* rec;
+    int c_wire;  // this lane's candidate (lanes below nc): wire, slope g, drift, cosa
+    float c_g, c_d, c_cosa;
+    int n, part, nf, nc, lane;
+    bool outside, over;
+    float eacc;
+    uint32_t flags;
+
+    // Best squared residual of `wire` below lambda (arguments equal on all
+    // lanes); Eq. 1 accumulates min(res^2, lambda) - lambda on top of H lambda.
+    __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r2) {
+        if (!(r2 < P.lam)) return;
+        for (int b = 0; b < nf; b += 32) {
+            const int i = b + lane;
+            const unsigned m = __ballot_sync(WARP_ALL, i < nf && (int)(rec->key[i] & 0xffffu) == wire);
+            if (m) {
+                const int k = b + __ffs(m) - 1;
+                const float old = rec->r2[k];
+                __syncwarp();
+                if (r2 < old) {
+                    eacc += r2 - old;
+                    if (lane == 0) {
+                        rec->r2[k] = r2;
+                        rec->key[k] = (uint32_t)wire | ((uint32_t)pt << 16);
+                    }
+                }
+                __syncwarp();
+                return;
+            }
+        }
+        eacc += r2 - P.lam;
+        if (nf < CDC_MAX_FOUND) {
+            if (lane == 0) {
+                rec->key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
+                rec->r2[nf] = r2;
+            }
+            ++nf;
+        } else {
+            flags |= CDC_FLAG_FOUND_OVERFLOW;
+        }
+        __syncwarp();
+    }
+
+    // Minima found by the lanes (r2 = +inf where none), recorded in lane order.
+    __device__ __forceinline__ void record_lanes(const ScanConst& P, float r2, int wire, int pt) {
+        unsigned m = __ballot_sync(WARP_ALL, r2 < P.lam);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            found(P, __shfl_sync(WARP_ALL, wire, src), pt, __shfl_sync(WARP_ALL, r2, src));
+        }
+    }
+
+    // Candidate list for the next LIST_M segments (the rules of Tracer::collect),
+    // candidate r on lane r.
+    __device__ __forceinline__ void rebuild(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                            const uchar2* s_tab) {
+        nc = 0;
+        over = false;
+        const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
+        const float rho = rho_of(x, y);
+        if (!in_chamber(s_tab, rho)) return;
+        const float wide = LIST_M * P.h;
+        const float reach = wide + 0.5f;
+        const float kap = fabsf(s.lam) * P.b_max;
+        const float bend = fmaf(0.5f * kap, reach * reach, 0.01f);
+        const float phi = atan2f(y, x);
+        for (int pass = 0;; ++pass) {
+            int wire;
+            float cosa;
+            const int tot = window_nth(s_lay, s_tab, fired, P.band + wide, P.d_win + wide, rho, phi, z,
+                                       pass * 32 + lane, wire, cosa);
+            bool keep = false;
+            float g = 0.f, d = 0.f;
+            if (wire >= 0) {
+                d = __ldg(dtab + wire);
+                if (d <= P.max_drift) {
+                    const float4 W = __ldg(G.wires + wire);
+                    float tp2;
+                    g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
+                    keep = tp2 < PARALLEL_T2;
+                    if (!keep && g < 0.f) {
+                        const float wp2 = point_doca2(x, y, z, W, cosa);
+                        const float lim = d + P.sqrt_lam + bend;
+                        keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, sqrt_ub(wp2)), tp2), g) + 1e-3f >= 0.f &&
+                               fmaf(wp2, tp2, -g * g) <= lim * lim * tp2;
+                    }
+                }
+            }
+            const unsigned kb = __ballot_sync(WARP_ALL, keep);
+            const int nk = __popc(kb);
+            const int r = lane - nc;
+            const bool take = r >= 0 && r < nk;
+            const int src = take ? (int)__fns(kb, 0, r + 1) : lane;
+            const int w2 = __shfl_sync(WARP_ALL, wire, src);
+            const float g2 = __shfl_sync(WARP_ALL, g, src), d2 = __shfl_sync(WARP_ALL, d, src),
+                        a2 = __shfl_sync(WARP_ALL, cosa, src);
+            if (take) {
+                c_wire = w2;
+                c_g = g2;
+                c_d = d2;
+                c_cosa = a2;
+            }
+            if (nc + nk > WARP_LIST_CAP) over = true;
+            nc = min(nc + nk, WARP_LIST_CAP);
+            if (tot <= (pass + 1) * 32) break;
+        }
+    }
+
+    // Seed state, the start-of-track minima and the first candidate list.
+    __device__ __forceinline__ void init(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                         const uchar2* s_tab, const float* dtab_, WarpFound* rec_, const float* sd) {
+        seed_state(sd, G.R0d, P.charge_dir, P.direction, s);
+        dtab = dtab_;
+        fired = (const uint32_t*)(dtab_ + G.n_wires);
+        rec = rec_;
+        lane = threadIdx.x & 31;
+        n = 0;
+        part = 0;
+        nf = 0;
+        nc = 0;
+        outside = true;
+        over = false;
+        eacc = 0.f;
+        flags = 0u;
+        c_wire = 0;
+        c_g = c_d = 0.f;
+        c_cosa = 1.f;
+        const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
+        const float rho = rho_of(x, y);
+        if (in_chamber(s_tab, rho)) {
+            const float phi = atan2f(y, x);
+            for (int pass = 0;; ++pass) {
+                int wire;
+                float cosa;
+                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, z, pass * 32 + lane, wire,
+                                           cosa);
+                float r2 = INFINITY;
+                if (wire >= 0) {
+                    const float d = __ldg(dtab + wire);
+                    if (d <= P.max_drift) {
+                        const float4 W = __ldg(G.wires + wire);
+                        float tp2;
+                        if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f) {
+                            const float r = point_doca(x, y, z, W, cosa) - d;
+                            r2 = r * r;
+                        }
+                    }
+                }
+                record_lanes(P, r2, wire, 0);
+                if (tot <= (pass + 1) * 32) break;
+            }
+        }
+        rebuild(G, P, s_lay, s_tab);
+    }
+
+    __device__ __forceinline__ void advance(const DevField& F, const ScanConst& P) {
+        ox = s.rx;
+        oy = s.ry;
+        oz = s.rz;
+        otx = s.tx;
+        oty = s.ty;
+        otz = s.tz;
+        rkn_step<KIND>(F, s, P.h, P.h6_lo);
+        ++n;
+    }
+
+    // Sign tests of the listed wires, one per lane.
+    __device__ __forceinline__ void list_pass(const DevGeom& G, const ScanConst& P) {
+        if (over) return;
+        float r2 = INFINITY;
+        if (lane < nc) {
+            const float4 W = __ldg(G.wires + c_wire);
+            float tp2;
+            const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, c_cosa, tp2);
+            if (c_g < 0.f && g1 >= 0.f)
+                r2 = seg_res2(P, fabsf(s.lam) * P.b_max, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty,
+                              s.tz, W, c_cosa, c_d, c_g, g1);
+            c_g = g1;
+        }
+        record_lanes(P, r2, c_wire, part);
+    }
+
+    // Window search when the list overflowed, turn bookkeeping, stop tests and
+    // the track-end minima (the rules of Tracer::finish); false once ended.
+    __device__ __forceinline__ bool finish(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                           const uchar2* s_tab) {
+        const float nx = s.rx, ny = s.ry, nz = s.rz, ntx = s.tx, nty = s.ty, ntz = s.tz;
+        const float rho = rho_of(nx, ny);
+        if (over && in_chamber(s_tab, rho)) {
+            const float kap = fabsf(s.lam) * P.b_max;
+            const float phi = atan2f(ny, nx);
+            for (int pass = 0;; ++pass) {
+                int wire;
+                float cosa;
+                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, pass * 32 + lane,
+                                           wire, cosa);
+                float r2 = INFINITY;
+                if (wire >= 0) {
+                    const float d = __ldg(dtab + wire);
+                    if (d <= P.max_drift) {
+                        const float4 W = __ldg(G.wires + wire);
+                        float tp2;
+                        const float g0 = dist_slope(ox, oy, oz, otx, oty, otz, W, cosa, tp2);
+                        if (g0 < 0.f) {
+                            const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2);
+                            if (g1 >= 0.f)
+                                r2 = seg_res2(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa, d,
+                                              g0, g1);
+                        }
+                    }
+                }
+                record_lanes(P, r2, wire, part);
+                if (tot <= (pass + 1) * 32) break;
+            }
+        }
+        const bool now_out = rho >= G.R0;
+        bool stop = false;
+        if (outside && !now_out) {
+            ++part;
+            if (part >= P.max_part) stop = true;
+        }
+        outside = now_out;
+        if (fabsf(nz) > G.z_half || rho > G.R_out) stop = true;
+        if (!stop && n >= P.max_steps) {
+            stop = true;
+            flags |= CDC_FLAG_STEP_CAP;
+        }
+        if (stop && part < P.max_part && in_chamber(s_tab, rho)) {
+            const float phi = atan2f(ny, nx);
+            for (int pass = 0;; ++pass) {
+                int wire;
+                float cosa;
+                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, pass * 32 + lane,
+                                           wire, cosa);
+                float r2 = INFINITY;
+                if (wire >= 0) {
+                    const float d = __ldg(dtab + wire);
+                    if (d <= P.max_drift) {
+                        const float4 W = __ldg(G.wires + wire);
+                        float tp2;
+                        if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
+                            const float r = point_doca(nx, ny, nz, W, cosa) - d;
+                            r2 = r * r;
+                        }
+                    }
+                }
+                record_lanes(P, r2, wire, part);
+                if (tot <= (pass + 1) * 32) break;
+            }
+        }
+        return !stop;
+    }
+
+    // The whole track of the seed; returns the number of steps.
+    __device__ __forceinline__ void run(const DevGeom& G, const DevField& F, const ScanConst& P, const DevLayer* s_lay,
+                                        const uchar2* s_tab) {
+        for (;;) {
+            advance(F, P);
+            list_pass(G, P);
+            if (!finish(G, P, s_lay, s_tab)) break;
+            if (n % LIST_M == 0) rebuild(G, P, s_lay, s_tab);
+        }
+    }
+
+    __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
+};
+
+}  // namespace cdc

@@ -55,7 +55,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.cdc_candidate) == 28
     assert C.sizeof(_lib.cdc_hough_params) == 13 * 4 + 60
     assert C.sizeof(_lib.cdc_refine_params) == 32
-    assert C.sizeof(_lib.cdc_scan_config) == 8
+    assert C.sizeof(_lib.cdc_scan_config) == 12
     # compile a probe against the header and compare sizes/offsets
     probe = r'''
 #include <stdio.h>
