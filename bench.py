@@ -437,8 +437,13 @@ def run_cuda(args, ws, rank, local):
         ctx.cdc_scan_seeds(ne, o, w, d, grid, sp, None, topk0, best_E, best_seed, hit_part, None, None, sflags,
                            steps, stream)
 
-    tuned, tune_ms = tr.tune(off, wid, dr, grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags,
-                                                            stream), sp, reps=3, stream=stream)
+    grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream)
+    if args.scan_shape:
+        tuned = tuple(int(x) for x in args.scan_shape.split(","))
+        ctx.cdc_set_scan_config(*tuned)
+        tune_ms = None
+    else:
+        tuned, tune_ms = tr.tune(off, wid, dr, grid, sp, reps=3, stream=stream)
     launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan fill+stage, 5/round, 9 zoom grids, assign
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     for _ in range(args.warmup):
@@ -645,6 +650,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=3, help="timed graph replays of the batched leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 30 %%-occupancy precision/scale leg")
     ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
+    ap.add_argument("--scan-shape", default=None,
+                    help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")
     ap.add_argument("--profile-case", action="store_true",
                     help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
     args = ap.parse_args()
