@@ -55,6 +55,21 @@ WORKLOAD = ("single multi-turn 104.97 MeV e- event, solenoid map 451x1001 @ 2 mm
             "hit classification of the best seed")
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
 SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune_scan's timings
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
+# single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
+# kernel sources it was taken on (SHA-256 over the csrc files), else reported as null.
+TRAFFIC = {"bytes": 33_138_176 + 14_306_560, "csrc_sha256": "ec90906cd442c9e34f37d457f1d329bb140f0c4ed2063ed731f668d7a420c42e"}
+
+
+def csrc_digest() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_1908_01949_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
 
 
@@ -546,7 +561,9 @@ def run_cuda(args, ws, rank, local):
                          "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None, "flops_per_rkn_step": f_step,
+                     "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
+                     "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
+                     "flops_per_rkn_step": f_step,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz (unit counts and max clock)"},
         "e2e": {"value": seeds_per_step / (e2e / 1e3), "unit": "seeds/s", "ms_per_step": e2e,
