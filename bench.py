@@ -255,7 +255,16 @@ def batched_leg(args, rank, local, g, fm, flush):
     ms, steps = time_graph(graph, out, flush, args.batched_steps)
     seeds_step = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
     fl = out["flags"].cpu().numpy()
+    # classification quality (sec. 3.1, Eqs. 2-3): the grids are centred on the first turn, so
+    # scan partition k is truth turn k
+    truth = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=tr.dev)
+    cls_counts = tr.classification_counts(off_t, out["hit_part"], truth, MAX_PART).cpu().numpy()
+    eps, pur = cdc.efficiency_purity(cls_counts)
     return {"events": n_ev, "coarse_seeds": n, "seeds_per_step": seeds_step,
+            "classification": {"partition": list(range(MAX_PART)),
+                               "efficiency": [None if np.isnan(x) else float(x) for x in eps],
+                               "purity": [None if np.isnan(x) else float(x) for x in pur],
+                               "definition": "Eqs. 2-3 summed over the events; scan partition k = truth turn k"},
             "coarse_seeds_min_max": [min(counts), max(counts)], "hits": int(wid.size), "ms_per_step": ms,
             "seeds_per_s": seeds_step / (ms / 1e3), "rkn_steps_per_s": steps / (ms / 1e3),
             "events_per_s": n_ev / (ms / 1e3), "graph": "one CUDA graph per step (all rounds, all events)",

@@ -294,6 +294,22 @@ int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int3
                   const cdc_grid* grids, const cdc_scan_params* params, int reps, cdc_scan_config* best, float* ms,
                   void* stream);
 
+/* ---- classification quality --------------------------------------------- */
+
+/* Counts for the classification efficiency and purity of sec. 3.1 (Eqs. 2-3):
+ * for every event e, counts[e][i + 1][j + 1] = number of hits with truth
+ * partition i classified as partition j (i, j in -1 .. n_part - 1; -1 is noise
+ * for the truth and "not classified" for the scan; labels outside that range
+ * count as -1).  With C_{i->j} = counts[e][i+1][j+1] and C_i its row sum over
+ * all j, Eq. 2 is eps_j = C_{j->j} / C_j and Eq. 3 is pi_j = C_{j->j} /
+ * sum_{i >= 0} C_{i->j}.  The caller aligns the truth labels with the scan's
+ * partition numbering (partition 0 = the turn of the scanned seed).  Device
+ * inputs: hit_off [n_events + 1], hit_part and truth_part [H] (int8); device
+ * output counts [n_events][n_part + 1][n_part + 1] (int32, overwritten).
+ * n_part 1..16.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_CUDA. */
+int cdc_classification_counts(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int8_t* hit_part,
+                              const int8_t* truth_part, int n_part, int32_t* counts, void* stream);
+
 /* ---- allocation-free scan ---------------------------------------------- */
 
 #define CDC_NOALLOC_MAX_EVENTS 8

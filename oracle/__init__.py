@@ -293,3 +293,38 @@ def chi2(g, f, params, wire_id, drift, part, seed, sigma=0.2):
     if rc:
         raise RuntimeError("orc_chi2 failed")
     return c2.value, gr, jtj.reshape(5, 5), nu.value, fl.value
+
+
+# ------------------------------------------------- classification quality
+def classification_counts(hit_off, hit_part, truth_part, n_part):
+    """Sec. 3.1: C[e, i + 1, j + 1] = number of hits of event e whose truth
+    partition is i and whose classified partition is j (i, j in -1 .. n_part-1;
+    -1 = noise / not classified; labels outside the range count as -1)."""
+    ne = len(hit_off) - 1
+    C = np.zeros((ne, n_part + 1, n_part + 1), np.int64)
+    for e in range(ne):
+        for h in range(hit_off[e], hit_off[e + 1]):
+            i, j = int(truth_part[h]), int(hit_part[h])
+            i = i + 1 if 0 <= i < n_part else 0
+            j = j + 1 if 0 <= j < n_part else 0
+            C[e, i, j] += 1
+    return C
+
+
+def efficiency_purity(C):
+    """Eq. 2, eps_n' = C_{n'->n'} / C_{n'} (C_{n'}: all hits of truth partition
+    n'), and Eq. 3, pi_n' = C_{n'->n'} / sum_{i=1..n} C_{i->n'} (over the
+    signal's partitions only), from counts C [..., n+1, n+1] summed over the
+    leading axes; NaN where the denominator is 0."""
+    C = np.asarray(C).reshape(-1, np.shape(C)[-2], np.shape(C)[-1]).sum(0)
+    n = C.shape[0] - 1
+    eps = np.full(n, np.nan)
+    pur = np.full(n, np.nan)
+    for k in range(n):
+        c_k = sum(C[k + 1, j] for j in range(n + 1))
+        to_k = sum(C[i + 1, k + 1] for i in range(n))
+        if c_k:
+            eps[k] = C[k + 1, k + 1] / c_k
+        if to_k:
+            pur[k] = C[k + 1, k + 1] / to_k
+    return eps, pur

@@ -15,7 +15,7 @@ from ._lib import (CAND_DTYPE, CDC_MAX_K, CDC_MAX_ZOOM, EXPORTS, FLAG_BAD_HIT, F
                    FLAG_FOUND_OVERFLOW, FLAG_LOST_HIT, FLAG_NOT_SPD, FLAG_STEP_CAP, GRID_BYTES, GRID_DTYPE, CdcError,
                    Context, grids_to_tensor, hough_params, lib, refine_params, scan_params, tensor_to_grids)
 
-__all__ = ["Context", "Tracker", "CdcError", "chi2", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
+__all__ = ["Context", "Tracker", "CdcError", "chi2", "efficiency_purity", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
            "tensor_to_grids", "GRID_DTYPE", "CAND_DTYPE", "EXPORTS", "lib"]
 
 
@@ -89,6 +89,15 @@ class Tracker:
         ne = int(hit_off.numel()) - 1
         return self.ctx.cdc_tune_scan(ne, hit_off, wire_id, drift, grids, params, reps, stream)
 
+    def classification_counts(self, hit_off, hit_part, truth_part, n_part, stream=None):
+        """Per-event counts [n_events, n_part + 1, n_part + 1] of (truth partition,
+        classified partition) pairs, index 0 = -1 (sec. 3.1, Eqs. 2-3)."""
+        t = self.torch
+        ne = int(hit_off.numel()) - 1
+        counts = t.empty((ne, n_part + 1, n_part + 1), dtype=t.int32, device=self.dev)
+        self.ctx.cdc_classification_counts(ne, hit_off, hit_part, truth_part, n_part, counts, stream)
+        return counts
+
     def propagate(self, seeds, params, every, n_rec, precision=0, stream=None):
         t = self.torch
         n = int(seeds.shape[0])
@@ -157,6 +166,19 @@ def chi2(tracker, seed_event, seeds, hit_off, wire_id, drift, scan, params):
     may require grad); the hit assignment of each seed is taken at the seed
     itself, as in cdc_chi2_grad."""
     return _chi2_function().apply(seeds, tracker, seed_event, hit_off, wire_id, drift, scan, params)
+
+
+def efficiency_purity(counts):
+    """Eqs. 2-3 of sec. 3.1 from classification counts [..., n+1, n+1] (index
+    0 = -1): eps[j] = C_{j->j} / C_j and pi[j] = C_{j->j} / sum_{i>=0} C_{i->j},
+    summed over any leading (event) axes; NaN where a denominator is 0."""
+    c = np.asarray(counts, dtype=np.float64)
+    c = c.reshape(-1, c.shape[-2], c.shape[-1]).sum(0)
+    diag = np.diagonal(c)[1:]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        eps = diag / c[1:, :].sum(1)
+        pur = diag / c[1:, 1:].sum(0)
+    return eps, pur
 
 
 def decode_candidates(t):

@@ -441,6 +441,20 @@ int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32
     return CDC_OK;
 }
 
+int cdc_classification_counts(cdc_ctx* c, int n_events, const int32_t* hit_off, const int8_t* hit_part,
+                              const int8_t* truth_part, int n_part, int32_t* counts, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (n_events < 0) return fail(c, CDC_ERR_ARG, "n_events < 0");
+    if (n_events == 0) return CDC_OK;
+    if (n_part < 1 || n_part > 16) return fail(c, CDC_ERR_RANGE, "n_part outside 1..16");
+    if (!hit_off || !hit_part || !truth_part || !counts) return fail(c, CDC_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_class_counts(n_events, hit_off, hit_part, truth_part, n_part, counts, c->num_sms,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "classification counts");
+    return CDC_OK;
+}
+
 static const cdc_scan_config SCAN_CONFIGS[CDC_SCAN_CONFIGS] = {{256, 16, 0}, {256, 32, 0}, {128, 16, 0}, {128, 32, 0}};
 
 int cdc_set_scan_config(cdc_ctx* c, const cdc_scan_config* cfg) {

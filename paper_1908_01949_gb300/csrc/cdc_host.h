@@ -61,6 +61,9 @@ cudaError_t launch_stage(const DevGeom& G, int n_events, const int32_t* hit_off,
 cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
                         const ScanLaunch& L, int num_sms, cudaStream_t st);
 
+cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8_t* hit_part,
+                                const int8_t* truth_part, int n_part, int32_t* counts, int num_sms, cudaStream_t st);
+
 cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
                              const float* seeds, int every, int n_rec, int precision, double* pos, int32_t* n_steps,
                              double* path, cudaStream_t st);

@@ -136,6 +136,15 @@ __global__ void prologue_kernel(int n_events, const cdc_grid* __restrict__ grids
     }
 }
 
+__device__ __forceinline__ int find_event_i32(const int32_t* off, int n, int i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int find_event(const long long* off, int n, long long i) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -493,6 +502,31 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
         if (hit_part) hit_part[h] = (int8_t)part;
         if (hit_res2) hit_res2[h] = r2;
     }
+}
+
+// ------------------------------------------------- classification counts
+// counts[e][truth + 1][class + 1] += 1 per hit (sec. 3.1, Eqs. 2-3).
+__global__ void class_counts_kernel(int n_events, const int32_t* __restrict__ hit_off,
+                                    const int8_t* __restrict__ hit_part, const int8_t* __restrict__ truth_part,
+                                    int n_part, int32_t* counts) {
+    const int total = hit_off[n_events];
+    const int np1 = n_part + 1;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < total; h += gridDim.x * blockDim.x) {
+        const int e = find_event_i32(hit_off, n_events, h);
+        int t = truth_part[h], c = hit_part[h];
+        t = (t < 0 || t >= n_part) ? 0 : t + 1;
+        c = (c < 0 || c >= n_part) ? 0 : c + 1;
+        atomicAdd(&counts[((size_t)e * np1 + t) * np1 + c], 1);
+    }
+}
+
+cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8_t* hit_part,
+                                const int8_t* truth_part, int n_part, int32_t* counts, int num_sms, cudaStream_t st) {
+    const size_t n = (size_t)n_events * (n_part + 1) * (n_part + 1);
+    cudaError_t e = cudaMemsetAsync(counts, 0, n * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    class_counts_kernel<<<num_sms * 2, 256, 0, st>>>(n_events, hit_off, hit_part, truth_part, n_part, counts);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ propagation
