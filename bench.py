@@ -274,6 +274,68 @@ def batched_leg(args, rank, local, g, fm, flush):
                                                               "L2 flushed before each"}
 
 
+def _gen_bidir(i):
+    import cdc_synth as S
+    return S.cfg2_case(20_000 + i, _GEN_FIELD, occupancy=0.10)[2]
+
+
+BIDIR_SEEDS = 100_000
+
+
+def bidirectional_leg(args, rank, local, g, fm, flush):
+    """Bidirectional scan (sec. 2.2): the first turn of each multi-turn event
+    scanned from its entrance (direction +1) and from its exit (direction -1),
+    ten rounds each, all events of a direction in one call, then N_c (hits in
+    partition 0 of both) per event and the N_c >= 20 cut.  Grids: the multi-turn
+    grid scaled to 10^5 seeds around each truth seed (random sub-step offset)."""
+    import multiprocessing as mp
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    n_ev = int(args.bidir_events)
+    with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 32), initializer=_gen_init) as pool:
+        evs = pool.map(_gen_bidir, range(1000 * rank, 1000 * rank + n_ev), chunksize=1)
+    rng = np.random.default_rng(11)
+    ent = np.concatenate([S.scaled_grid(e.truth_seeds[0], BIDIR_SEEDS, rng) for e in evs])
+    ext = np.concatenate([S.scaled_grid(e.exit_seeds[0], BIDIR_SEEDS, rng) for e in evs])
+    for gr, e in zip(ext, evs):                      # the exit seed's (z0, pz0) is not at 0: centre them too
+        gr["centre"][1], gr["centre"][4] = e.exit_seeds[0][1], e.exit_seeds[0][4]
+    for gr, e in zip(ent, evs):
+        gr["centre"][1], gr["centre"][4] = e.truth_seeds[0][1], e.truth_seeds[0][4]
+    off, wid, dr = S.pack_events(evs)
+    n_seeds = max(int(sum(np.prod(gr["n"]) for gr in ent)), int(sum(np.prod(gr["n"]) for gr in ext)))
+    tr = cdc.Tracker(g, fm, device=local, max_events=n_ev, max_seeds=n_seeds, max_hits=int(wid.size))
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    ps = [cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=1, direction=d, k=K, n_rounds=N_ROUNDS,
+                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT) for d in (1, -1)]
+    gts = [cdc.grids_to_tensor(ent, tr.dev), cdc.grids_to_tensor(ext, tr.dev)]
+
+    def run():
+        outs = [tr.scan(off_t, wid_t, dr_t, gt, p) for gt, p in zip(gts, ps)]
+        return outs, tr.common_hits(off_t, outs[0]["hit_part"], outs[1]["hit_part"])
+
+    for _ in range(max(args.warmup, 1)):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        outs, nc = run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    nc = nc.cpu().numpy()
+    turn0 = np.array([int(np.sum(e.truth_part == 0)) for e in evs])
+    return {"events": n_ev, "seeds_per_direction": n_seeds, "ms": ms, "events_per_s": n_ev / (ms / 1e3),
+            "seeds_per_s": 2 * (n_seeds + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev) / (ms / 1e3),
+            "n_common_mean": float(nc.mean()), "n_common_min": int(nc.min()),
+            "pass_nc_ge_20": float(np.mean(nc >= 20)), "turn0_hits_mean": float(turn0.mean()),
+            "timing": "median of 3: both directions' ten-round scans and the N_c kernel"}
+
+
 SWEEP_EVERY, SWEEP_REC, SWEEP_SEEDS = 250, 12, 10_000
 
 
@@ -543,6 +605,9 @@ def run_cuda(args, ws, rank, local):
     sweep = None
     if not args.no_sweep and not args.profile_case:
         sweep = sweep_leg(args, rank, local, g, fm, flush)
+    bidir = None
+    if not args.no_bidir and not args.profile_case:
+        bidir = bidirectional_leg(args, rank, local, g, fm, flush)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
@@ -566,6 +631,7 @@ def run_cuda(args, ws, rank, local):
         "refine": refine,
         "batched": batched,
         "sweep": sweep,
+        "bidirectional": bidir,
         "events_per_s": {"scan": ws / (ms / 1e3),
                          "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
@@ -676,6 +742,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=3, help="timed graph replays of the batched leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 30 %%-occupancy precision/scale leg")
     ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
+    ap.add_argument("--no-bidir", action="store_true", help="skip the bidirectional-scan leg")
+    ap.add_argument("--bidir-events", type=int, default=32, help="events of the bidirectional leg")
     ap.add_argument("--scan-shape", default=None,
                     help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")
     ap.add_argument("--profile-case", action="store_true",

@@ -274,8 +274,27 @@ def turn_labels(pos: np.ndarray, R0: float):
     return lab, np.nonzero(outward)[0]
 
 
+def inward_crossings(pos: np.ndarray, R0: float):
+    """Sample indices i with an inward R0 crossing between samples i and i + 1."""
+    rho = np.hypot(pos[:, 0], pos[:, 1])
+    return np.nonzero((rho[1:] < R0) & (rho[:-1] >= R0))[0]
+
+
+def exit_seeds(pos, dirs, outward, R0, p):
+    """Per turn (started at the outward crossings `outward`), the state at the
+    first inward R0 crossing after its start, or NaN."""
+    inw = inward_crossings(pos, R0)
+    out = np.full((len(outward), 5), np.nan)
+    for k, c in enumerate(outward):
+        after = inw[inw > c]
+        end = outward[k + 1] if k + 1 < len(outward) else len(pos)
+        if after.size and after[0] < end:
+            out[k] = crossing_seed(pos, dirs, int(after[0]), R0, p)
+    return out
+
+
 def crossing_seed(pos, dirs, i, R0, p):
-    """Truth seed (theta0, z0, px0, py0, pz0) at the outward R0 crossing in (i, i+1)."""
+    """Truth seed (theta0, z0, px0, py0, pz0) at the R0 crossing in (i, i+1)."""
     r1 = math.hypot(pos[i, 0], pos[i, 1])
     r2 = math.hypot(pos[i + 1, 0], pos[i + 1, 1])
     w = (R0 - r1) / (r2 - r1)
@@ -345,6 +364,10 @@ class Event:
     n_turns: int
     signal_p0: np.ndarray = field(default_factory=lambda: np.zeros(3))
     signal_r0: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    # float64[n_turns, 5]: state at the inward R0 crossing that ends each turn
+    # (momentum along the motion; NaN for a turn that leaves through an end
+    # plate), the seed of the reversed scan of that turn
+    exit_seeds: np.ndarray = field(default_factory=lambda: np.zeros((0, 5)))
 
 
 def _iso_dir(rng):
@@ -391,7 +414,7 @@ def _signal(g, f, rng, turns, max_tries=20000, min_hits=20, p=SIGNAL_P, max_hits
         if len(hits) < min_hits or (max_hits is not None and len(hits) > max_hits):
             continue
         seeds = np.array([crossing_seed(pos, dirs, i, g.R0, p) for i in cr])
-        return hits, seeds, len(cr), r0, p * t
+        return hits, seeds, len(cr), r0, p * t, exit_seeds(pos, dirs, cr, g.R0, p)
     raise RuntimeError("signal generation failed")
 
 
@@ -426,7 +449,7 @@ def make_event(g: Geometry, f: Field, rng: np.random.Generator, turns=(1,),
     with drift U[0, max_drift]; noise='dio': DIO-like tracks up to `occupancy`
     of all wires."""
     wm, wd, _ = wire_lines(g)
-    hits, seeds, nt, r0, p0 = _signal(g, f, rng, turns, min_hits=min_hits, max_hits=max_hits)
+    hits, seeds, nt, r0, p0, xseeds = _signal(g, f, rng, turns, min_hits=min_hits, max_hits=max_hits)
     wires = sorted(hits)
     drift = [min(max(hits[w][0] + rng.normal(0.0, sigma), 0.0), max_drift) for w in wires]
     part = [hits[w][1] for w in wires]
@@ -448,7 +471,8 @@ def make_event(g: Geometry, f: Field, rng: np.random.Generator, turns=(1,),
     return Event(wire_id=np.asarray(wires, dtype=np.int32)[order],
                  drift=np.asarray(drift, dtype=np.float32)[order],
                  truth_part=np.asarray(part, dtype=np.int8)[order],
-                 truth_seeds=seeds, n_turns=nt, signal_p0=np.asarray(p0), signal_r0=np.asarray(r0))
+                 truth_seeds=seeds, n_turns=nt, signal_p0=np.asarray(p0), signal_r0=np.asarray(r0),
+                 exit_seeds=xseeds)
 
 
 def pack_events(events):

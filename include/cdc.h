@@ -310,6 +310,17 @@ int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int3
 int cdc_classification_counts(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int8_t* hit_part,
                               const int8_t* truth_part, int n_part, int32_t* counts, void* stream);
 
+/* Hits found by both directions of the bidirectional scan (sec. 2.2: the scan
+ * runs independently on seeds at the entrance and at the exit of a partition,
+ * direction +1 and -1, and a track needs N_c >= 20 common hits): n_common[e] =
+ * number of hits h of event e with part_a[h] == pa and part_b[h] == pb, where
+ * part_a, part_b are the hit_part outputs of the two scans (for the turn
+ * scanned from both ends, pa = pb = 0).  Device inputs hit_off [n_events + 1],
+ * part_a, part_b [H] (int8); device output n_common [n_events] (int32).
+ * Errors: CDC_ERR_ARG, CDC_ERR_CUDA. */
+int cdc_common_hits(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int8_t* part_a, const int8_t* part_b,
+                    int pa, int pb, int32_t* n_common, void* stream);
+
 /* ---- allocation-free scan ---------------------------------------------- */
 
 #define CDC_NOALLOC_MAX_EVENTS 8

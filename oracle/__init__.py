@@ -328,3 +328,10 @@ def efficiency_purity(C):
         if to_k:
             pur[k] = C[k + 1, k + 1] / to_k
     return eps, pur
+
+
+def common_hits(hit_off, part_a, part_b, pa=0, pb=0):
+    """Sec. 2.2 (bidirectional scan): per event the number of hits classified
+    pa by the scan in one direction and pb by the scan in the other."""
+    return np.array([sum(1 for h in range(hit_off[e], hit_off[e + 1]) if part_a[h] == pa and part_b[h] == pb)
+                     for e in range(len(hit_off) - 1)], np.int64)

@@ -98,6 +98,15 @@ class Tracker:
         self.ctx.cdc_classification_counts(ne, hit_off, hit_part, truth_part, n_part, counts, stream)
         return counts
 
+    def common_hits(self, hit_off, part_a, part_b, pa=0, pb=0, stream=None):
+        """N_c per event: hits classified pa by one scan and pb by the other
+        (sec. 2.2, bidirectional scan)."""
+        t = self.torch
+        ne = int(hit_off.numel()) - 1
+        n = t.empty(ne, dtype=t.int32, device=self.dev)
+        self.ctx.cdc_common_hits(ne, hit_off, part_a, part_b, pa, pb, n, stream)
+        return n
+
     def propagate(self, seeds, params, every, n_rec, precision=0, stream=None):
         t = self.torch
         n = int(seeds.shape[0])

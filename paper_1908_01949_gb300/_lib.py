@@ -35,7 +35,7 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
-           "cdc_classification_counts", "cdc_scan_seeds_noalloc"]
+           "cdc_classification_counts", "cdc_common_hits", "cdc_scan_seeds_noalloc"]
 
 
 class cdc_grid(C.Structure):
@@ -113,6 +113,7 @@ def lib():
                                              vp, vp, vp, vp]
         L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
         L.cdc_classification_counts.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, vp]
+        L.cdc_common_hits.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, vp, vp]
         L.cdc_set_scan_config.argtypes = [vp, P(cdc_scan_config)]
         L.cdc_get_scan_config.argtypes = [vp, P(cdc_scan_config)]
         L.cdc_tune_scan.argtypes = [vp, C.c_int, vp, vp, vp, vp, P(cdc_scan_params), C.c_int, P(cdc_scan_config),
@@ -314,6 +315,14 @@ class Context:
         return self._check(self.L.cdc_classification_counts(
             self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(hit_part, torch.int8, "hit_part", d),
             _dev(truth_part, torch.int8, "truth_part", d), int(n_part), _dev(counts, torch.int32, "counts", d),
+            _stream(stream)))
+
+    def cdc_common_hits(self, n_events, hit_off, part_a, part_b, pa, pb, n_common, stream=None):
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_common_hits(
+            self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(part_a, torch.int8, "part_a", d),
+            _dev(part_b, torch.int8, "part_b", d), int(pa), int(pb), _dev(n_common, torch.int32, "n_common", d),
             _stream(stream)))
 
     def cdc_set_scan_config(self, block, chunk, warp_seeds=None):

@@ -455,6 +455,19 @@ int cdc_classification_counts(cdc_ctx* c, int n_events, const int32_t* hit_off, 
     return CDC_OK;
 }
 
+int cdc_common_hits(cdc_ctx* c, int n_events, const int32_t* hit_off, const int8_t* part_a, const int8_t* part_b,
+                    int pa, int pb, int32_t* n_common, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (n_events < 0) return fail(c, CDC_ERR_ARG, "n_events < 0");
+    if (n_events == 0) return CDC_OK;
+    if (!hit_off || !part_a || !part_b || !n_common) return fail(c, CDC_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_common_hits(n_events, hit_off, part_a, part_b, pa, pb, n_common, c->num_sms,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "common hits");
+    return CDC_OK;
+}
+
 static const cdc_scan_config SCAN_CONFIGS[CDC_SCAN_CONFIGS] = {{256, 16, 0}, {256, 32, 0}, {128, 16, 0}, {128, 32, 0}};
 
 int cdc_set_scan_config(cdc_ctx* c, const cdc_scan_config* cfg) {

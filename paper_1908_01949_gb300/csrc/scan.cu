@@ -520,6 +520,34 @@ __global__ void class_counts_kernel(int n_events, const int32_t* __restrict__ hi
     }
 }
 
+// n_common[e] = hits of event e classified pa by one scan and pb by the other.
+__global__ void common_hits_kernel(int n_events, const int32_t* __restrict__ hit_off,
+                                   const int8_t* __restrict__ part_a, const int8_t* __restrict__ part_b, int pa,
+                                   int pb, int32_t* n_common) {
+    for (int e = blockIdx.x; e < n_events; e += gridDim.x) {
+        int c = 0;
+        for (int h = hit_off[e] + threadIdx.x; h < hit_off[e + 1]; h += blockDim.x)
+            c += (part_a[h] == pa && part_b[h] == pb) ? 1 : 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+        __shared__ int s_c[8];
+        if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_c[w];
+            n_common[e] = t;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_common_hits(int n_events, const int32_t* hit_off, const int8_t* part_a, const int8_t* part_b,
+                               int pa, int pb, int32_t* n_common, int num_sms, cudaStream_t st) {
+    common_hits_kernel<<<std::min(n_events, num_sms * 8), 256, 0, st>>>(n_events, hit_off, part_a, part_b, pa, pb,
+                                                                       n_common);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8_t* hit_part,
                                 const int8_t* truth_part, int n_part, int32_t* counts, int num_sms, cudaStream_t st) {
     const size_t n = (size_t)n_events * (n_part + 1) * (n_part + 1);
