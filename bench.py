@@ -336,6 +336,52 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
             "timing": "median of 3: both directions' ten-round scans and the N_c kernel"}
 
 
+SPLIT_PZ, SPLIT_CHUNK = 4, 32768
+
+
+def split_ab_leg(args, rank, local, g, fm, ev, grid_t, flush):
+    """The coarse round of the multi-turn event on a reduced grid (4 pz0 values,
+    160000 seeds) by the fused scan and by the paper's two-kernel organisation
+    (states recorded by a thread per seed, then a block per seed and a thread
+    per hit), timed with CUDA events; the scores agree to float rounding."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    gg = cdc.tensor_to_grids(grid_t).copy()
+    gg["n"][0][4] = SPLIT_PZ
+    n = int(np.prod(gg["n"][0]))
+    tr = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=n, max_hits=4096)
+    tr.ctx.cdc_reserve_split(args.split_chunk, MAX_STEPS)
+    tr.ctx.cdc_set_scan_config(256, 16)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    gt = cdc.grids_to_tensor(gg, tr.dev)
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=1,
+                         max_drift=MAX_DRIFT)
+    E = torch.empty(n, dtype=torch.float32, device=tr.dev)
+    flags = torch.empty(1, dtype=torch.int32, device=tr.dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+    ms_f, fused = timed(lambda: tr.scan(off, wid, dr, gt, sp, want_E=True, want_hits=False, n_seeds=n))
+    ms_s, _ = timed(lambda: tr.ctx.cdc_scan_seeds_split(1, n, off, wid, dr, gt, sp, E, flags))
+    Ef, Es = fused["E"].cpu().numpy(), E.cpu().numpy()
+    return {"seeds": n, "fused_ms": ms_f, "split_ms": ms_s, "fused_seeds_per_s": n / (ms_f / 1e3),
+            "split_seeds_per_s": n / (ms_s / 1e3), "speedup_fused_over_split": ms_s / ms_f,
+            "max_rel_score_diff": float(np.max(np.abs(Es - Ef) / np.maximum(np.abs(Ef), 1e-30))),
+            "split_chunk": args.split_chunk, "timing": "median of 3 single-round calls, L2 flushed before each"}
+
+
 SWEEP_EVERY, SWEEP_REC, SWEEP_SEEDS = 250, 12, 10_000
 
 
@@ -605,6 +651,9 @@ def run_cuda(args, ws, rank, local):
     sweep = None
     if not args.no_sweep and not args.profile_case:
         sweep = sweep_leg(args, rank, local, g, fm, flush)
+    split_ab = None
+    if not args.no_split and not args.profile_case:
+        split_ab = split_ab_leg(args, rank, local, g, fm, ev, grid, flush)
     bidir = None
     if not args.no_bidir and not args.profile_case:
         bidir = bidirectional_leg(args, rank, local, g, fm, flush)
@@ -632,6 +681,7 @@ def run_cuda(args, ws, rank, local):
         "batched": batched,
         "sweep": sweep,
         "bidirectional": bidir,
+        "split_ab": split_ab,
         "events_per_s": {"scan": ws / (ms / 1e3),
                          "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
@@ -743,6 +793,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 30 %%-occupancy precision/scale leg")
     ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
     ap.add_argument("--no-bidir", action="store_true", help="skip the bidirectional-scan leg")
+    ap.add_argument("--no-split", action="store_true", help="skip the two-kernel A/B leg")
+    ap.add_argument("--split-chunk", type=int, default=SPLIT_CHUNK, help="seeds recorded at a time by the A/B leg")
     ap.add_argument("--bidir-events", type=int, default=32, help="events of the bidirectional leg")
     ap.add_argument("--scan-shape", default=None,
                     help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")

@@ -294,6 +294,31 @@ int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int3
                   const cdc_grid* grids, const cdc_scan_params* params, int reps, cdc_scan_config* best, float* ms,
                   void* stream);
 
+/* ---- the paper's two-kernel scan (A/B reference) ------------------------ */
+
+/* Workspace of cdc_scan_seeds_split: room for the recorded states of `chunk`
+ * seeds with up to max_steps steps (2 x 16 B per step and seed).  Errors:
+ * CDC_ERR_ARG, CDC_ERR_RANGE (chunk outside 1..2^20, max_steps outside
+ * 1..6900), CDC_ERR_NOMEM. */
+int cdc_reserve_split(cdc_ctx* ctx, int chunk, int max_steps);
+
+/* The coarse scan organised as in the paper's "kernel function separation"
+ * (sec. 3): for `chunk` seeds at a time, kernel A (one thread per seed) records
+ * the state after every RKN step to the end of the track, then kernel B (one
+ * block per seed, threads over the event's hits: the block-per-seed,
+ * thread-per-wire layout of sec. 2.2) finds every hit's distance of closest
+ * approach from the recorded states and sums Eq. 1.  Same minima and scores as
+ * cdc_scan_seeds (up to the order of the Eq. 1 sum), one round only, scores
+ * only: E [n_seeds] (device, float32, by row-major seed index), flags
+ * [n_events].  n_seeds must equal the grids' total seed count (seeds beyond
+ * the true total are skipped, their E left unwritten); duplicate wires in an
+ * event (flagged CDC_FLAG_BAD_HIT) are scored per hit here.  params->max_steps
+ * must not exceed the reserved max_steps.  Errors as cdc_scan_seeds, plus
+ * CDC_ERR_NOT_LOADED (no cdc_reserve_split). */
+int cdc_scan_seeds_split(cdc_ctx* ctx, int n_events, int64_t n_seeds, const int32_t* hit_off,
+                         const int32_t* wire_id, const float* drift, const cdc_grid* grids,
+                         const cdc_scan_params* params, float* E, uint32_t* flags, void* stream);
+
 /* ---- classification quality --------------------------------------------- */
 
 /* Counts for the classification efficiency and purity of sec. 3.1 (Eqs. 2-3):

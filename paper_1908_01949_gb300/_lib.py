@@ -35,7 +35,8 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
-           "cdc_classification_counts", "cdc_common_hits", "cdc_scan_seeds_noalloc"]
+           "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_classification_counts", "cdc_common_hits",
+           "cdc_scan_seeds_noalloc"]
 
 
 class cdc_grid(C.Structure):
@@ -113,6 +114,8 @@ def lib():
                                              vp, vp, vp, vp]
         L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
         L.cdc_classification_counts.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, vp]
+        L.cdc_reserve_split.argtypes = [vp, C.c_int, C.c_int]
+        L.cdc_scan_seeds_split.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp]
         L.cdc_common_hits.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, vp, vp]
         L.cdc_set_scan_config.argtypes = [vp, P(cdc_scan_config)]
         L.cdc_get_scan_config.argtypes = [vp, P(cdc_scan_config)]
@@ -316,6 +319,19 @@ class Context:
             self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(hit_part, torch.int8, "hit_part", d),
             _dev(truth_part, torch.int8, "truth_part", d), int(n_part), _dev(counts, torch.int32, "counts", d),
             _stream(stream)))
+
+    def cdc_reserve_split(self, chunk, max_steps):
+        return self._check(self.L.cdc_reserve_split(self.h, int(chunk), int(max_steps)))
+
+    def cdc_scan_seeds_split(self, n_events, n_seeds, hit_off, wire_id, drift, grids, params, E, flags, stream=None):
+        """The paper's two-kernel scan (record states, then DOCA per hit): scores only."""
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_scan_seeds_split(
+            self.h, int(n_events), int(n_seeds), _dev(hit_off, torch.int32, "hit_off", d),
+            _dev(wire_id, torch.int32, "wire_id", d), _dev(drift, torch.float32, "drift", d),
+            _dev(grids, torch.uint8, "grids", d), C.byref(params), _dev(E, torch.float32, "E", d),
+            _dev(flags, torch.int32, "flags", d), _stream(stream)))
 
     def cdc_common_hits(self, n_events, hit_off, part_a, part_b, pa, pb, n_common, stream=None):
         import torch

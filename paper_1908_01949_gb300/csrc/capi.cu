@@ -40,6 +40,11 @@ struct cdc_ctx {
     int2* d_offsets = nullptr;
     size_t offsets_cap = 0;
     int off_key[4] = {-1, -1, -1, -1};
+    // the two-kernel scan's recorded states (cdc_reserve_split)
+    float4 *split_r = nullptr, *split_t = nullptr;
+    int* split_n = nullptr;
+    int8_t* split_end = nullptr;
+    int split_chunk = 0, split_steps = 0;
     // scan-kernel launch shape (cdc_scan_config)
     int scan_block = 256, scan_chunk = 16, scan_warp_seeds = 0;
     // kernel timer
@@ -177,6 +182,10 @@ void cdc_destroy(cdc_ctx* c) {
     dfree(c->d_cells);
     dfree(c->d_offsets);
     free_workspace(c->W);
+    dfree(c->split_r);
+    dfree(c->split_t);
+    dfree(c->split_n);
+    dfree(c->split_end);
     for (cudaEvent_t e : c->timer_ev) cudaEventDestroy(e);
     delete c;
 }
@@ -452,6 +461,57 @@ int cdc_classification_counts(cdc_ctx* c, int n_events, const int32_t* hit_off, 
     cudaError_t e = launch_class_counts(n_events, hit_off, hit_part, truth_part, n_part, counts, c->num_sms,
                                         (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "classification counts");
+    return CDC_OK;
+}
+
+int cdc_reserve_split(cdc_ctx* c, int chunk, int max_steps) {
+    if (!c) return CDC_ERR_ARG;
+    if (chunk < 1 || chunk > (1 << 20) || max_steps < 1 || max_steps > 6900)
+        return fail(c, CDC_ERR_RANGE, "split reserve: chunk outside 1..2^20 or max_steps outside 1..6900");
+    DeviceGuard g(c->device);
+    dfree(c->split_r);
+    dfree(c->split_t);
+    dfree(c->split_n);
+    dfree(c->split_end);
+    c->split_chunk = c->split_steps = 0;
+    const size_t n = (size_t)chunk * (max_steps + 1);
+    cudaError_t e;
+    if ((e = dalloc(c->split_r, n)) != cudaSuccess || (e = dalloc(c->split_t, n)) != cudaSuccess ||
+        (e = dalloc(c->split_n, (size_t)chunk)) != cudaSuccess || (e = dalloc(c->split_end, (size_t)chunk)) != cudaSuccess)
+        return fail(c, CDC_ERR_NOMEM, std::string("split workspace: ") + cudaGetErrorString(e));
+    c->split_chunk = chunk;
+    c->split_steps = max_steps;
+    return CDC_OK;
+}
+
+int cdc_scan_seeds_split(cdc_ctx* c, int n_events, int64_t n_seeds, const int32_t* hit_off, const int32_t* wire_id,
+                         const float* drift, const cdc_grid* grids, const cdc_scan_params* p, float* E,
+                         uint32_t* flags, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (n_events < 0 || n_seeds < 0) return fail(c, CDC_ERR_ARG, "n_events or n_seeds < 0");
+    if (n_events == 0) return CDC_OK;
+    cdc_scan_params p1 = *p;
+    p1.n_rounds = 1;
+    int rc = check_scan_params(c, &p1, true);
+    if (rc) return rc;
+    if (!hit_off || !wire_id || !drift || !grids || !E || !flags) return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (n_events > c->W.max_events || c->W.n_wires < c->G.n_wires)
+        return fail(c, CDC_ERR_NOT_LOADED, "workspace too small: call cdc_reserve");
+    if (!c->split_r || p->max_steps > c->split_steps)
+        return fail(c, CDC_ERR_NOT_LOADED, "split workspace missing or max_steps above its reserve");
+    if (n_seeds > c->W.e_cap) return fail(c, CDC_ERR_RANGE, "n_seeds above the reserved seed capacity");
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_events, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flags reset");
+    const ScanConst P = make_const(c, &p1);
+    if ((e = launch_stage(c->G, n_events, hit_off, wire_id, drift, P.max_drift, c->W.drift_tab, flags, c->num_sms,
+                          st)) != cudaSuccess)
+        return cuda_fail(c, e, "staging");
+    SplitLaunch L{n_events, hit_off, wire_id, drift, grids, n_seeds, c->split_chunk, 256, c->W, flags, E,
+                  c->split_r, c->split_t, c->split_n, c->split_end};
+    if ((e = launch_split(c->G, c->F, P, L, st)) != cudaSuccess) return cuda_fail(c, e, "split scan launch");
     return CDC_OK;
 }
 

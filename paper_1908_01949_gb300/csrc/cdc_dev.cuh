@@ -300,6 +300,56 @@ __device__ __forceinline__ long long grid_count(const cdc_grid& g) {
     return c;
 }
 
+// ------------------------------------------------- events and seed grids
+__device__ __forceinline__ int find_event_i32(const int32_t* off, int n, int i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_event(const long long* off, int n, long long i) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The q-th seed of event e in scan order (scan_order_index within each of the
+// event's grids): its values, and its row-major index among the event's seeds.
+__device__ __forceinline__ long long event_seed_ordered(const cdc_grid* grids, int gpe, int e, long long q,
+                                                       float* sd) {
+    long long base = 0;
+    for (int g = 0; g < gpe; ++g) {
+        const cdc_grid& gr = grids[(size_t)e * gpe + g];
+        const long long c = grid_count(gr);
+        if (q < c || g == gpe - 1) {
+            const long long li = scan_order_index(gr, q);
+            grid_seed(gr, li, sd);
+            return base + li;
+        }
+        q -= c;
+        base += c;
+    }
+    return base;
+}
+
+__device__ __forceinline__ void event_seed(const cdc_grid* grids, int gpe, int e, long long local, float* sd) {
+    for (int g = 0; g < gpe; ++g) {
+        const cdc_grid& gr = grids[(size_t)e * gpe + g];
+        long long c = grid_count(gr);
+        if (local < c || g == gpe - 1) {
+            grid_seed(gr, local, sd);
+            return;
+        }
+        local -= c;
+    }
+}
+
 __device__ __forceinline__ uint64_t make_key(float e, uint32_t idx) {
     uint32_t b = __float_as_uint(e);
     if (!(e >= 0.f)) b = 0x7f800000u;  // NaN or negative cannot occur; order them last

@@ -53,6 +53,11 @@ struct ScanLaunch {
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.
 
+// Seed offsets of every event (W.seed_off), the seed total and a reset work
+// counter (W.counters) for grids with gpe grids per event.
+cudaError_t launch_seed_offsets(int n_events, const cdc_grid* grids, int gpe, const Workspace& W, uint32_t* flags,
+                                cudaStream_t st);
+
 // Fills the per-event hit tables of n_events events from the CSR hit lists;
 // flags (nullable) receives CDC_FLAG_BAD_HIT for invalid or duplicate hits.
 cudaError_t launch_stage(const DevGeom& G, int n_events, const int32_t* hit_off, const int32_t* wire_id,
@@ -70,6 +75,27 @@ cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8
 cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
                              const float* seeds, int every, int n_rec, int precision, double* pos, int32_t* n_steps,
                              double* path, cudaStream_t st);
+
+// The paper's two-kernel scan (split.cu): record states, then DOCA per hit.
+struct SplitLaunch {
+    int n_events;
+    const int32_t* hit_off;
+    const int32_t* wire_id;
+    const float* drift;
+    const cdc_grid* grids;  // one per event
+    long long n_seeds;      // the grids' total
+    int chunk;              // seeds recorded at a time
+    int block;              // threads per seed block of the DOCA kernel
+    Workspace W;
+    uint32_t* flags;
+    float* E;
+    float4* rec_r;          // [chunk][max_steps + 1]
+    float4* rec_t;
+    int* n_rec;             // [chunk]
+    int8_t* end_ok;         // [chunk]
+};
+cudaError_t launch_split(const DevGeom& G, const DevField& F, const ScanConst& P, const SplitLaunch& L,
+                         cudaStream_t st);
 
 // Hough (hough.cu).
 struct HoughLaunch {

@@ -136,55 +136,6 @@ __global__ void prologue_kernel(int n_events, const cdc_grid* __restrict__ grids
     }
 }
 
-__device__ __forceinline__ int find_event_i32(const int32_t* off, int n, int i) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int find_event(const long long* off, int n, long long i) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// The q-th seed of event e in scan order (scan_order_index within each of the
-// event's grids): its values, and its row-major index among the event's seeds.
-__device__ __forceinline__ long long event_seed_ordered(const cdc_grid* grids, int gpe, int e, long long q,
-                                                       float* sd) {
-    long long base = 0;
-    for (int g = 0; g < gpe; ++g) {
-        const cdc_grid& gr = grids[(size_t)e * gpe + g];
-        const long long c = grid_count(gr);
-        if (q < c || g == gpe - 1) {
-            const long long li = scan_order_index(gr, q);
-            grid_seed(gr, li, sd);
-            return base + li;
-        }
-        q -= c;
-        base += c;
-    }
-    return base;
-}
-
-__device__ __forceinline__ void event_seed(const cdc_grid* grids, int gpe, int e, long long local, float* sd) {
-    for (int g = 0; g < gpe; ++g) {
-        const cdc_grid& gr = grids[(size_t)e * gpe + g];
-        long long c = grid_count(gr);
-        if (local < c || g == gpe - 1) {
-            grid_seed(gr, local, sd);
-            return;
-        }
-        local -= c;
-    }
-}
-
 // ------------------------------------------------------------- the scan
 struct ScanIO {
     const float* drift_tab;
@@ -699,6 +650,13 @@ template <int KIND>
 static ScanKernel scan_kernel_of(int block, int chunk) {
     if (block == 128) return chunk == 32 ? scan_kernel<KIND, 128, 32> : scan_kernel<KIND, 128, 16>;
     return chunk == 32 ? scan_kernel<KIND, 256, 32> : scan_kernel<KIND, 256, 16>;
+}
+
+cudaError_t launch_seed_offsets(int n_events, const cdc_grid* grids, int gpe, const Workspace& W, uint32_t* flags,
+                                cudaStream_t st) {
+    prologue_kernel<<<1, 1024, 0, st>>>(n_events, grids, gpe, W.e_cap, W.seg_cap, W.seed_off, W.seg_off, W.counters,
+                                        flags);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P, const Workspace& W,
