@@ -336,6 +336,57 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
             "timing": "median of 3: both directions' ten-round scans and the N_c kernel"}
 
 
+def event_loop_leg(args, rank, local, g, fm):
+    """The event loop over turn partitions (sec. 2.3, Fig. 7) on multi-turn
+    events: a scan around the first turn (10^5 seeds; the synthetic events have
+    no trigger counter that would single out the last turn), then refine,
+    extrapolation to the neighbouring turns and narrow scans until fewer than
+    ten hits remain.
+    Wall-clock per event (the loop waits for each step); efficiency and purity
+    per truth turn (Eqs. 2-3) from the library's counting kernel."""
+    import multiprocessing as mp
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    from paper_1908_01949_gb300.event_loop import align_to_truth, event_loop, findable_truth
+    n_ev = int(args.loop_events)
+    with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 32), initializer=_gen_init) as pool:
+        evs = pool.map(_gen_bidir, range(5000 + 1000 * rank, 5000 + 1000 * rank + n_ev), chunksize=1)
+    tr = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=BIDIR_SEEDS, max_hits=4096)
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=1, k=K, n_rounds=N_ROUNDS,
+                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    rp = cdc.refine_params(n_iter=REFINE_ITER, sigma=REFINE_SIGMA, checkpoint=REFINE_CKPT)
+    rng = np.random.default_rng(13)
+    grids = []
+    for e in evs:
+        gr = S.scaled_grid(e.truth_seeds[0], BIDIR_SEEDS, rng)
+        gr["centre"][0][1], gr["centre"][0][4] = e.truth_seeds[0][1], e.truth_seeds[0][4]
+        grids.append(gr)
+    event_loop(tr, evs[0].wire_id, evs[0].drift, grids[0], sp, rp)          # warm-up
+    torch.cuda.synchronize()
+    n_turns = max(e.n_turns for e in evs)
+    counts = np.zeros((n_turns + 1, n_turns + 1), np.int64)
+    found = []
+    t0 = time.perf_counter()
+    for e, gr in zip(evs, grids):
+        labels, seeds = event_loop(tr, e.wire_id, e.drift, gr, sp, rp)
+        aligned = align_to_truth(labels, e.truth_part)
+        dev = tr.dev
+        c = tr.classification_counts(torch.tensor([0, e.wire_id.size], dtype=torch.int32, device=dev),
+                                     torch.as_tensor(aligned, device=dev),
+                                     torch.as_tensor(findable_truth(e.truth_part), device=dev), n_turns)
+        counts += c[0].cpu().numpy()
+        found.append(len(seeds))
+    wall = time.perf_counter() - t0
+    eps, pur = cdc.efficiency_purity(counts)
+    return {"events": n_ev, "ms_per_event": 1e3 * wall / n_ev, "events_per_s": n_ev / wall,
+            "turns_found_mean": float(np.mean(found)), "truth_turns_mean": float(np.mean([e.n_turns for e in evs])),
+            "efficiency_per_turn": [None if np.isnan(x) else float(x) for x in eps],
+            "purity_per_turn": [None if np.isnan(x) else float(x) for x in pur],
+            "truth": "turns of fewer than 10 hits (never taken as a turn by the loop) count as noise",
+            "timing": "host wall clock over the events (each step waits for the GPU)"}
+
+
 SPLIT_PZ, SPLIT_CHUNK = 4, 32768
 
 
@@ -651,6 +702,9 @@ def run_cuda(args, ws, rank, local):
     sweep = None
     if not args.no_sweep and not args.profile_case:
         sweep = sweep_leg(args, rank, local, g, fm, flush)
+    loop = None
+    if not args.no_loop and not args.profile_case:
+        loop = event_loop_leg(args, rank, local, g, fm)
     split_ab = None
     if not args.no_split and not args.profile_case:
         split_ab = split_ab_leg(args, rank, local, g, fm, ev, grid, flush)
@@ -682,6 +736,7 @@ def run_cuda(args, ws, rank, local):
         "sweep": sweep,
         "bidirectional": bidir,
         "split_ab": split_ab,
+        "event_loop": loop,
         "events_per_s": {"scan": ws / (ms / 1e3),
                          "refine": ws * refine["events_per_s"] if refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
@@ -794,6 +849,8 @@ def main():
     ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
     ap.add_argument("--no-bidir", action="store_true", help="skip the bidirectional-scan leg")
     ap.add_argument("--no-split", action="store_true", help="skip the two-kernel A/B leg")
+    ap.add_argument("--no-loop", action="store_true", help="skip the event-loop leg")
+    ap.add_argument("--loop-events", type=int, default=16, help="events of the event-loop leg")
     ap.add_argument("--split-chunk", type=int, default=SPLIT_CHUNK, help="seeds recorded at a time by the A/B leg")
     ap.add_argument("--bidir-events", type=int, default=32, help="events of the bidirectional leg")
     ap.add_argument("--scan-shape", default=None,

@@ -319,6 +319,24 @@ int cdc_scan_seeds_split(cdc_ctx* ctx, int n_events, int64_t n_seeds, const int3
                          const int32_t* wire_id, const float* drift, const cdc_grid* grids,
                          const cdc_scan_params* params, float* E, uint32_t* flags, void* stream);
 
+/* ---- the event loop over turn partitions ------------------------------- */
+
+/* Seed of the neighbouring turn partition (sec. 2.3: the seeds of the previous
+ * partition are predicted by extrapolating the fitted track backwards; the
+ * flowchart of Fig. 7 repeats this partition by partition).  For each seed (a
+ * turn's state at its outward R0 crossing) the track is propagated with the
+ * scan's step h (the FP32 refine stepper) in `direction` (-1: back to the
+ * previous turn, +1: on to the next) to its second change of side of the R0
+ * cylinder (starting inside for -1, outside for +1); the crossing point and
+ * direction are interpolated linearly in rho between the two states around
+ * it, the point projected onto the cylinder: seeds_out [n_seeds][5] (float32,
+ * momentum along the forward motion, |p| kept; NaN where none).  status
+ * [n_seeds]: 0 found, 1 the track left |z| <= z_half or rho <= R_out first, 2
+ * max_steps reached.  scan supplies h, max_steps and charge.  Device arrays.
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
+int cdc_extrapolate_turn(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_params* scan, int direction,
+                         float* seeds_out, int32_t* status, void* stream);
+
 /* ---- classification quality --------------------------------------------- */
 
 /* Counts for the classification efficiency and purity of sec. 3.1 (Eqs. 2-3):

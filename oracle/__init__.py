@@ -81,6 +81,7 @@ def lib():
             _lib.orc_hough_peaks.argtypes = [P(Geometry), P(HoughParams), C.c_int, ip, fp, fp, dp]
             _lib.orc_refine.argtypes = [P(Geometry), P(Field), P(ScanParams), C.c_int, C.c_double, dp, C.c_int,
                                         ip, dp, ip, dp, dp, dp, dp, ip, ip]
+            _lib.orc_extrapolate_turn.argtypes = [P(Geometry), P(Field), P(ScanParams), dp, C.c_int, dp]
             _lib.orc_chi2.argtypes = [P(Geometry), P(Field), P(ScanParams), C.c_double, C.c_int, ip, dp, ip, dp,
                                       dp, dp, dp, ip, ip]
         return _lib
@@ -335,3 +336,18 @@ def common_hits(hit_off, part_a, part_b, pa=0, pb=0):
     pa by the scan in one direction and pb by the scan in the other."""
     return np.array([sum(1 for h in range(hit_off[e], hit_off[e + 1]) if part_a[h] == pa and part_b[h] == pb)
                      for e in range(len(hit_off) - 1)], np.int64)
+
+
+# ------------------------------------------------------- neighbouring turn
+def extrapolate_turn(g, f, seed, params: ScanParams, direction):
+    """Sec. 2.3: seed of the previous (direction -1) or next (+1) turn partition
+    from the seed of a turn: (seed float64[5], status 0 found / 1 left the
+    chamber / 2 step limit)."""
+    L = lib()
+    keep = _Keep()
+    G, F = _geom(g, keep), _field(f, keep)
+    s = keep.arr(seed, np.float64)
+    out = np.zeros(5)
+    st = L.orc_extrapolate_turn(C.byref(G), C.byref(F), C.byref(params), _p(s, C.c_double), int(direction),
+                                _p(out, C.c_double))
+    return out, int(st)

@@ -851,3 +851,54 @@ int orc_chi2(const orc_geometry* g, const orc_field* f, const orc_scan_params* P
     free(tst);
     return 0;
 }
+
+/* ------------------------------------------- the neighbouring turn (sec. 2.3) */
+/* Seed of the neighbouring turn partition, for the event loop of sec. 2.3 (the
+ * seeds of the previous partition are predicted by extrapolating the fitted
+ * track backwards).  From the seed s of a turn (its state at the outward R0
+ * crossing), the track is propagated with steps of h in `direction` (-1: back
+ * in time, +1: forward).  Its side of the R0 cylinder starts as inside for -1
+ * (the reversed track moves inwards) and outside for +1; at the second change
+ * of side the crossing point and direction are interpolated linearly between
+ * the two states around it (in rho), the point is projected onto the cylinder,
+ * and out = (theta0, z0, p t) with t along the forward motion and |p| kept.
+ * Returns 0, 1 if the track first leaves |z| <= z_half or rho <= R_out, 2 if
+ * max_steps steps pass. */
+int orc_extrapolate_turn(const orc_geometry* g, const orc_field* f, const orc_scan_params* P0, const double s[5],
+                         int direction, double out[5]) {
+    orc_scan_params P = *P0;
+    P.direction = direction < 0 ? -1 : 1;
+    double r[3], t[3], lam, rn[3], tn[3];
+    orc_seed_state(g, &P, s, r, t, &lam, NULL);
+    const double p = sqrt(s[2] * s[2] + s[3] * s[3] + s[4] * s[4]);
+    int outside = P.direction > 0, changes = 0;
+    for (int n = 0; n < P.max_steps; ++n) {
+        orc_rkn_step(f, lam, P.h, r, t, rn, tn);
+        const double rho0 = hypot(r[0], r[1]), rho1 = hypot(rn[0], rn[1]);
+        const int now_out = rho1 >= g->R0;
+        if (now_out != outside) {
+            outside = now_out;
+            if (++changes == 2) {
+                const double w = (g->R0 - rho0) / (rho1 - rho0);
+                double q[3], d[3];
+                for (int a = 0; a < 3; ++a) {
+                    q[a] = r[a] + w * (rn[a] - r[a]);
+                    d[a] = t[a] + w * (tn[a] - t[a]);
+                }
+                const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const double sc = g->R0 / hypot(q[0], q[1]);
+                const double sign = P.direction < 0 ? -1.0 : 1.0;
+                out[0] = atan2(q[1] * sc, q[0] * sc);
+                out[1] = q[2];
+                for (int a = 0; a < 3; ++a) out[2 + a] = sign * p * d[a] / dn;
+                return 0;
+            }
+        }
+        if (fabs(rn[2]) > g->z_half || rho1 > g->R_out) return 1;
+        for (int a = 0; a < 3; ++a) {
+            r[a] = rn[a];
+            t[a] = tn[a];
+        }
+    }
+    return 2;
+}

@@ -98,6 +98,16 @@ class Tracker:
         self.ctx.cdc_classification_counts(ne, hit_off, hit_part, truth_part, n_part, counts, stream)
         return counts
 
+    def extrapolate_turn(self, seeds, params, direction, stream=None):
+        """Seeds of the previous (-1) or next (+1) turn partition (sec. 2.3):
+        (seeds [n, 5] float32, status [n] int32)."""
+        t = self.torch
+        n = int(seeds.shape[0])
+        out = t.empty((n, 5), dtype=t.float32, device=self.dev)
+        st = t.empty(n, dtype=t.int32, device=self.dev)
+        self.ctx.cdc_extrapolate_turn(n, seeds, params, direction, out, st, stream)
+        return out, st
+
     def common_hits(self, hit_off, part_a, part_b, pa=0, pb=0, stream=None):
         """N_c per event: hits classified pa by one scan and pb by the other
         (sec. 2.2, bidirectional scan)."""

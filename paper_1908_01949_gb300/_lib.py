@@ -35,7 +35,8 @@ STATUS = {0: "CDC_OK", -1: "CDC_ERR_ARG", -2: "CDC_ERR_RANGE", -3: "CDC_ERR_CUDA
 EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "cdc_load_field", "cdc_reserve",
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
-           "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_classification_counts", "cdc_common_hits",
+           "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_extrapolate_turn", "cdc_classification_counts",
+           "cdc_common_hits",
            "cdc_scan_seeds_noalloc"]
 
 
@@ -115,6 +116,7 @@ def lib():
         L.cdc_kernel_time.argtypes = [vp, P(C.c_double), P(C.c_int64), vp, C.c_int]
         L.cdc_classification_counts.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, vp]
         L.cdc_reserve_split.argtypes = [vp, C.c_int, C.c_int]
+        L.cdc_extrapolate_turn.argtypes = [vp, C.c_int, vp, P(cdc_scan_params), C.c_int, vp, vp, vp]
         L.cdc_scan_seeds_split.argtypes = [vp, C.c_int, i64, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp]
         L.cdc_common_hits.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, C.c_int, vp, vp]
         L.cdc_set_scan_config.argtypes = [vp, P(cdc_scan_config)]
@@ -319,6 +321,13 @@ class Context:
             self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(hit_part, torch.int8, "hit_part", d),
             _dev(truth_part, torch.int8, "truth_part", d), int(n_part), _dev(counts, torch.int32, "counts", d),
             _stream(stream)))
+
+    def cdc_extrapolate_turn(self, n_seeds, seeds, scan, direction, seeds_out, status, stream=None):
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_extrapolate_turn(
+            self.h, int(n_seeds), _dev(seeds, torch.float32, "seeds", d), C.byref(scan), int(direction),
+            _dev(seeds_out, torch.float32, "seeds_out", d), _dev(status, torch.int32, "status", d), _stream(stream)))
 
     def cdc_reserve_split(self, chunk, max_steps):
         return self._check(self.L.cdc_reserve_split(self.h, int(chunk), int(max_steps)))

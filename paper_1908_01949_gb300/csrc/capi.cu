@@ -515,6 +515,27 @@ int cdc_scan_seeds_split(cdc_ctx* c, int n_events, int64_t n_seeds, const int32_
     return CDC_OK;
 }
 
+int cdc_extrapolate_turn(cdc_ctx* c, int n_seeds, const float* seeds, const cdc_scan_params* p, int direction,
+                         float* seeds_out, int32_t* status, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
+    if (n_seeds < 0) return fail(c, CDC_ERR_ARG, "n_seeds < 0");
+    if (n_seeds == 0) return CDC_OK;
+    if (direction != 1 && direction != -1) return fail(c, CDC_ERR_ARG, "direction must be +1 or -1");
+    if (!p) return fail(c, CDC_ERR_ARG, "scan params is NULL");
+    cdc_scan_params p1 = *p;
+    p1.direction = direction;
+    p1.n_rounds = 1;
+    int rc = check_scan_params(c, &p1, false);
+    if (rc) return rc;
+    if (!seeds || !seeds_out || !status) return fail(c, CDC_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_extrapolate_turn(c->G, c->F, make_const(c, &p1), n_seeds, seeds, seeds_out, status,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "extrapolation launch");
+    return CDC_OK;
+}
+
 int cdc_common_hits(cdc_ctx* c, int n_events, const int32_t* hit_off, const int8_t* part_a, const int8_t* part_b,
                     int pa, int pb, int32_t* n_common, void* stream) {
     if (!c) return CDC_ERR_ARG;

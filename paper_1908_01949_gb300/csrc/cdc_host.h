@@ -69,6 +69,9 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
 cudaError_t launch_common_hits(int n_events, const int32_t* hit_off, const int8_t* part_a, const int8_t* part_b,
                                int pa, int pb, int32_t* n_common, int num_sms, cudaStream_t st);
 
+cudaError_t launch_extrapolate_turn(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
+                                    const float* seeds, float* out, int32_t* status, cudaStream_t st);
+
 cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8_t* hit_part,
                                 const int8_t* truth_part, int n_part, int32_t* counts, int num_sms, cudaStream_t st);
 

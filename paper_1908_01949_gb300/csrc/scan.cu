@@ -508,6 +508,69 @@ cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- neighbouring turn (sec. 2.3)
+// Seed of the previous (direction -1) or next (+1) turn from the seed of a
+// turn: propagate (refine stepper) to the second change of side of the R0
+// cylinder (starting inside for -1, outside for +1), interpolate the crossing
+// linearly in rho between the two states, project it onto the cylinder and
+// return the momentum along the forward motion.  FP64 for the interpolation.
+template <int KIND>
+__global__ void extrapolate_turn_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds, const float* __restrict__ seeds,
+                                        float* out, int32_t* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seeds) return;
+    const int direction = P.direction;
+    float sd[5];
+    for (int a = 0; a < 5; ++a) sd[a] = seeds[(size_t)i * 5 + a];
+    State s;
+    seed_state(sd, G.R0d, P.charge_dir, direction, s);
+    const double p = sqrt((double)sd[2] * sd[2] + (double)sd[3] * sd[3] + (double)sd[4] * sd[4]);
+    bool outside = direction > 0;
+    int changes = 0, st = 2;
+    for (int n = 0; n < P.max_steps; ++n) {
+        const double x0 = (double)s.rx + s.lx, y0 = (double)s.ry + s.ly, z0 = (double)s.rz + s.lz;
+        const double tx0 = (double)s.tx + s.mx, ty0 = (double)s.ty + s.my, tz0 = (double)s.tz + s.mz;
+        rkn_step<KIND, true>(F, s, P.h, P.h6_lo);
+        const double x1 = (double)s.rx + s.lx, y1 = (double)s.ry + s.ly, z1 = (double)s.rz + s.lz;
+        const double rho0 = sqrt(x0 * x0 + y0 * y0), rho1 = sqrt(x1 * x1 + y1 * y1);
+        const bool now_out = rho1 >= G.R0d;
+        if (now_out != outside) {
+            outside = now_out;
+            if (++changes == 2) {
+                const double w = (G.R0d - rho0) / (rho1 - rho0);
+                const double qx = x0 + w * (x1 - x0), qy = y0 + w * (y1 - y0), qz = z0 + w * (z1 - z0);
+                const double dx = tx0 + w * ((double)s.tx + s.mx - tx0), dy = ty0 + w * ((double)s.ty + s.my - ty0),
+                             dz = tz0 + w * ((double)s.tz + s.mz - tz0);
+                const double dn = sqrt(dx * dx + dy * dy + dz * dz), sign = direction < 0 ? -1.0 : 1.0;
+                out[(size_t)i * 5 + 0] = (float)atan2(qy, qx);
+                out[(size_t)i * 5 + 1] = (float)qz;
+                out[(size_t)i * 5 + 2] = (float)(sign * p * dx / dn);
+                out[(size_t)i * 5 + 3] = (float)(sign * p * dy / dn);
+                out[(size_t)i * 5 + 4] = (float)(sign * p * dz / dn);
+                st = 0;
+                break;
+            }
+        }
+        if (fabs(z1) > G.z_half || rho1 > G.R_out) {
+            st = 1;
+            break;
+        }
+    }
+    if (st != 0)
+        for (int a = 0; a < 5; ++a) out[(size_t)i * 5 + a] = __int_as_float(0x7fc00000);
+    status[i] = st;
+}
+
+cudaError_t launch_extrapolate_turn(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
+                                    const float* seeds, float* out, int32_t* status, cudaStream_t st) {
+    const int bs = 128, nb = (n_seeds + bs - 1) / bs;
+    if (F.kind == 0)
+        extrapolate_turn_kernel<0><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, out, status);
+    else
+        extrapolate_turn_kernel<1><<<nb, bs, 0, st>>>(G, F, P, n_seeds, seeds, out, status);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ propagation
 template <int KIND, bool LAM2>
 __global__ void propagate_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds, const float* __restrict__ seeds,

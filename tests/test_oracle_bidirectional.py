@@ -60,3 +60,24 @@ def test_common_hits_counts():
     b = [0, 1, 0, 1, 0, -1, 0, 2]
     assert O.common_hits(off, a, b).tolist() == [2, 0, 1]
     assert O.common_hits(off, a, b, 1, 1).tolist() == [1, 0, 0]
+
+
+def test_extrapolated_turns_reproduce_the_generator_seeds():
+    """Sec. 2.3: the seed of the previous / next turn extrapolated by the oracle
+    (RKN, h = 2 mm) equals the generator's truth seed of that turn (its own RK4
+    at 1 mm, interpolated at the crossing) to 2e-3 mm in z0 and 1e-3 MeV/c."""
+    fm = S.solenoid_map()
+    P = O.scan_params(h=2.0, max_steps=5000)
+    checked = 0
+    for index in range(4):
+        g, f, ev = S.cfg2_case(index, fm, occupancy=0.05)
+        ts = ev.truth_seeds
+        for k in range(len(ts)):
+            for direction, j in ((-1, k - 1), (1, k + 1)):
+                if 0 <= j < len(ts):
+                    out, st = O.extrapolate_turn(g, f, ts[k], P, direction)
+                    assert st == 0
+                    assert abs(out[0] - ts[j][0]) < 1e-5 and abs(out[1] - ts[j][1]) < 2e-3, (out, ts[j])
+                    assert np.all(np.abs(out[2:] - ts[j][2:]) < 1e-3), (out, ts[j])
+                    checked += 1
+    assert checked >= 10
