@@ -148,6 +148,17 @@ def grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags, strea
     return grid
 
 
+def guarded(name, fn):
+    """Run one secondary leg; a failure is reported in its place instead of
+    losing the benchmark line."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - the leg's error is the report
+        import traceback
+        traceback.print_exc()
+        return {"error": f"{name}: {type(e).__name__}: {e}"}
+
+
 def reduce_max(value: float, dist=None, device=None) -> float:
     """Max over ranks of a per-rank time: the slowest rank sets the step time."""
     if dist is None:
@@ -591,76 +602,130 @@ def run_cuda(args, ws, rank, local):
         tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
     seeds_coarse = int(np.prod(tmpl["n"][0]))
     seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
-    tr = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
     hp = cdc.hough_params(grid_template=tmpl)
     sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
-    stream = torch.cuda.current_stream()
     off_h = torch.tensor([0, ev.wire_id.size], dtype=torch.int32).pin_memory()
     wid_h = torch.from_numpy(ev.wire_id.astype(np.int32)).pin_memory()
     dr_h = torch.from_numpy(ev.drift.astype(np.float32)).pin_memory()
-    off, wid, dr = off_h.to(dev), wid_h.to(dev), dr_h.to(dev)
-    nh = wid.numel()
+    nh = int(wid_h.numel())
     ne = 1
-    acc = torch.empty((ne, hp.n_bins, hp.n_bins), dtype=torch.int32, device=dev)
-    cand = torch.empty((ne, hp.max_cand, 28), dtype=torch.uint8, device=dev)
-    ncand = torch.empty(ne, dtype=torch.int32, device=dev)
-    grid = torch.empty((ne, cdc.GRID_BYTES), dtype=torch.uint8, device=dev)
-    hflags = torch.empty(ne, dtype=torch.int32, device=dev)
-    best_E = torch.empty((ne, K), dtype=torch.float32, device=dev)
-    best_seed = torch.empty((ne, K, 5), dtype=torch.float32, device=dev)
-    topk0 = torch.empty((ne, K), dtype=torch.int64, device=dev)
-    hit_part = torch.empty(nh, dtype=torch.int8, device=dev)
-    sflags = torch.empty(ne, dtype=torch.int32, device=dev)
-    steps = torch.zeros(N_ROUNDS, dtype=torch.int64, device=dev)
-    ctx = tr.ctx
+    n_in = max(1, int(args.inflight))
 
-    def step(o, w, d):
-        ctx.cdc_hough_seeds(ne, o, w, hp, acc, cand, ncand, grid, hflags, stream)
-        ctx.cdc_scan_seeds(ne, o, w, d, grid, sp, None, topk0, best_E, best_seed, hit_part, None, None, sflags,
-                           steps, stream)
+    def make_slot(k):
+        """One event in flight: its own context (workspace), stream and buffers."""
+        t = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
+        d = dict(tr=t, ctx=t.ctx, stream=torch.cuda.current_stream() if k == 0 else torch.cuda.Stream(device=dev),
+                 off=off_h.to(dev), wid=wid_h.to(dev), dr=dr_h.to(dev),
+                 acc=torch.empty((ne, hp.n_bins, hp.n_bins), dtype=torch.int32, device=dev),
+                 cand=torch.empty((ne, hp.max_cand, 28), dtype=torch.uint8, device=dev),
+                 ncand=torch.empty(ne, dtype=torch.int32, device=dev),
+                 grid=torch.empty((ne, cdc.GRID_BYTES), dtype=torch.uint8, device=dev),
+                 hflags=torch.empty(ne, dtype=torch.int32, device=dev),
+                 best_E=torch.empty((ne, K), dtype=torch.float32, device=dev),
+                 best_seed=torch.empty((ne, K, 5), dtype=torch.float32, device=dev),
+                 topk0=torch.empty((ne, K), dtype=torch.int64, device=dev),
+                 hit_part=torch.empty(nh, dtype=torch.int8, device=dev),
+                 sflags=torch.empty(ne, dtype=torch.int32, device=dev),
+                 steps=torch.zeros(N_ROUNDS, dtype=torch.int64, device=dev),
+                 out_E=torch.empty((ne, K), dtype=torch.float32).pin_memory(),
+                 out_S=torch.empty((ne, K, 5), dtype=torch.float32).pin_memory(),
+                 out_P=torch.empty(nh, dtype=torch.int8).pin_memory(),
+                 out_F=torch.empty(ne, dtype=torch.int32).pin_memory())
+        return d
 
-    grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream)
+    slots = [make_slot(k) for k in range(n_in)]
+    tr, ctx, stream = slots[0]["tr"], slots[0]["ctx"], slots[0]["stream"]
+    off, wid, dr, grid = slots[0]["off"], slots[0]["wid"], slots[0]["dr"], slots[0]["grid"]
+
+    def step(q, h2d=False, d2h=False):
+        """One event through the hot path on slot q's stream; with h2d / d2h the
+        inputs come from pinned host memory and the results go back to it."""
+        st = q["stream"]
+        with torch.cuda.stream(st):
+            if h2d:
+                q["off"].copy_(off_h, non_blocking=True)
+                q["wid"].copy_(wid_h, non_blocking=True)
+                q["dr"].copy_(dr_h, non_blocking=True)
+            q["ctx"].cdc_hough_seeds(ne, q["off"], q["wid"], hp, q["acc"], q["cand"], q["ncand"], q["grid"],
+                                     q["hflags"], st)
+            q["ctx"].cdc_scan_seeds(ne, q["off"], q["wid"], q["dr"], q["grid"], sp, None, q["topk0"], q["best_E"],
+                                    q["best_seed"], q["hit_part"], None, None, q["sflags"], q["steps"], st)
+            if d2h:
+                q["out_E"].copy_(q["best_E"], non_blocking=True)
+                q["out_S"].copy_(q["best_seed"], non_blocking=True)
+                q["out_P"].copy_(q["hit_part"], non_blocking=True)
+                q["out_F"].copy_(q["sflags"], non_blocking=True)
+
+    grid_for_tuning(ctx, ne, off, wid, hp, slots[0]["acc"], slots[0]["cand"], slots[0]["ncand"], grid,
+                    slots[0]["hflags"], stream)
     if args.scan_shape:
         tuned = tuple(int(x) for x in args.scan_shape.split(","))
-        ctx.cdc_set_scan_config(*tuned)
         tune_ms = None
     else:
         tuned, tune_ms = tr.tune(off, wid, dr, grid, sp, reps=3, stream=stream)
-    launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan fill+stage, 5/round, 9 zoom grids, assign
+    for q in slots:
+        q["ctx"].cdc_set_scan_config(*tuned)
+    launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan clear+stage, 5/round, 9 zoom grids, assign
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    for _ in range(args.warmup):
-        step(off, wid, dr)
+    for i in range(args.warmup * n_in):
+        step(slots[i % n_in])
     torch.cuda.synchronize()
-    steps.zero_()
+
+    # latency and the roofline: one event at a time on one stream, the library's
+    # CUDA events around every scan-kernel launch
+    q0 = slots[0]
+    q0["steps"].zero_()
+    ctx.cdc_kernel_timer(True)
+    lat_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(q0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat_ms.append(e0.elapsed_time(e1))
+    ktot, kn, kper = ctx.cdc_kernel_time()
+    ctx.cdc_kernel_timer(False)
+    rkn = q0["steps"].cpu().numpy().astype(np.float64)
+    coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
+    coarse_steps = float(rkn[0]) / args.steps
+    latency = statistics.median(lat_ms)
+
+    # throughput: a stream of events, n_in of them in flight (one context and
+    # stream each, round robin); every step is one event's whole hot path
+    def run_stream(h2d=False, d2h=False):
+        main = torch.cuda.current_stream()
+        for q in slots:
+            q["steps"].zero_()
+            q["stream"].wait_stream(main)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(main)
+        for i in range(args.steps):
+            q = slots[i % n_in]
+            with torch.cuda.stream(q["stream"]):
+                flush.zero_()
+            step(q, h2d, d2h)
+        for q in slots:
+            main.wait_stream(q["stream"])
+        e1.record(main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3
+
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ctx.cdc_kernel_timer(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev_s[i].record(stream)
-        step(off, wid, dr)
-        ev_e[i].record(stream)
-    torch.cuda.synchronize()
+    dev_ms, wall = run_stream()
     if dist:
         dist.barrier()
-    wall = time.perf_counter() - t0
     clocks = sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(ev_s, ev_e)]
-    ktot, kn, kper = ctx.cdc_kernel_time()
-    ctx.cdc_kernel_timer(False)
-    ms = reduce_max(sum(step_ms) / len(step_ms), dist, dev)
-    rkn = steps.cpu().numpy().astype(np.float64)
-    rkn_per_step = float(rkn.sum()) / args.steps
-    coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
-    coarse_steps = float(rkn[0]) / args.steps
+    ms = reduce_max(dev_ms / args.steps, dist, dev)
+    rkn_per_step = float(sum(q["steps"].sum().item() for q in slots)) / args.steps
     # roofline of the dominant kernel (coarse-round scan launch), ALU bound
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -668,49 +733,33 @@ def run_cuda(args, ws, rank, local):
     f_step = flops_per_step(1)
     achieved = f_step * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12 if coarse_ms else None
 
-    # end to end: host inputs -> device, the step, results -> host (pinned)
-    out_E = torch.empty((ne, K), dtype=torch.float32).pin_memory()
-    out_S = torch.empty((ne, K, 5), dtype=torch.float32).pin_memory()
-    out_P = torch.empty(nh, dtype=torch.int8).pin_memory()
-    out_F = torch.empty(ne, dtype=torch.int32).pin_memory()
-    e2e_ms = []
-    off2, wid2, dr2 = torch.empty_like(off), torch.empty_like(wid), torch.empty_like(dr)
-    for i in range(max(3, min(args.steps, 10))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        off2.copy_(off_h, non_blocking=True)
-        wid2.copy_(wid_h, non_blocking=True)
-        dr2.copy_(dr_h, non_blocking=True)
-        step(off2, wid2, dr2)
-        out_E.copy_(best_E, non_blocking=True)
-        out_S.copy_(best_seed, non_blocking=True)
-        out_P.copy_(hit_part, non_blocking=True)
-        out_F.copy_(sflags, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    e2e = statistics.median(e2e_ms)
+    # end to end: the same stream of events with each step's inputs copied from
+    # pinned host memory and its results (best seeds and scores, hit classes,
+    # flags) copied back inside the timed region; host wall clock
+    _, e2e_wall = run_stream(h2d=True, d2h=True)
+    e2e = e2e_wall / args.steps
     h2d = int(off_h.numel() * 4 + wid_h.numel() * 4 + dr_h.numel() * 4)
-    d2h = int(out_E.numel() * 4 + out_S.numel() * 4 + out_P.numel() + out_F.numel() * 4)
+    d2h = int(q0["out_E"].numel() * 4 + q0["out_S"].numel() * 4 + q0["out_P"].numel() + q0["out_F"].numel() * 4)
+    wall = wall / 1e3
 
     refine = None
     if not args.no_refine and not args.profile_case:
-        refine = refine_leg(args, rank, local, g, fm, stream)
+        refine = guarded('refine', lambda: refine_leg(args, rank, local, g, fm, stream))
     batched = None
     if not args.no_batched and not args.profile_case:
-        batched = batched_leg(args, rank, local, g, fm, flush)
+        batched = guarded('batched', lambda: batched_leg(args, rank, local, g, fm, flush))
     sweep = None
     if not args.no_sweep and not args.profile_case:
-        sweep = sweep_leg(args, rank, local, g, fm, flush)
+        sweep = guarded('sweep', lambda: sweep_leg(args, rank, local, g, fm, flush))
     loop = None
     if not args.no_loop and not args.profile_case:
-        loop = event_loop_leg(args, rank, local, g, fm)
+        loop = guarded('loop', lambda: event_loop_leg(args, rank, local, g, fm))
     split_ab = None
     if not args.no_split and not args.profile_case:
-        split_ab = split_ab_leg(args, rank, local, g, fm, ev, grid, flush)
+        split_ab = guarded('split_ab', lambda: split_ab_leg(args, rank, local, g, fm, ev, grid, flush))
     bidir = None
     if not args.no_bidir and not args.profile_case:
-        bidir = bidirectional_leg(args, rank, local, g, fm, flush)
+        bidir = guarded('bidir', lambda: bidirectional_leg(args, rank, local, g, fm, flush))
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
@@ -723,14 +772,16 @@ def run_cuda(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "seeds_per_step": seeds_per_step, "events_per_step": 1,
+                   "events_in_flight": n_in,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"event-parallel x{ws} (independent events per GPU, no collective)"},
         "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
+        "latency_ms_per_event": latency,
         "coarse_scan": {"launch_ms": statistics.mean(coarse_ms) if coarse_ms else None, "rkn_steps": coarse_steps,
                         "seeds": seeds_coarse},
         "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]},
                      "shapes": [{"block": b, "chunk": c} for b, c in SCAN_SHAPES], "coarse_round_ms": tune_ms},
-        "refine_seeds_per_s": refine["seeds_per_s"] if refine else None,
+        "refine_seeds_per_s": refine.get("seeds_per_s") if refine else None,
         "refine": refine,
         "batched": batched,
         "sweep": sweep,
@@ -738,7 +789,7 @@ def run_cuda(args, ws, rank, local):
         "split_ab": split_ab,
         "event_loop": loop,
         "events_per_s": {"scan": ws / (ms / 1e3),
-                         "refine": ws * refine["events_per_s"] if refine else None},
+                         "refine": ws * refine["events_per_s"] if refine and "events_per_s" in refine else None},
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
@@ -855,6 +906,8 @@ def main():
     ap.add_argument("--bidir-events", type=int, default=32, help="events of the bidirectional leg")
     ap.add_argument("--scan-shape", default=None,
                     help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="events in flight (one context and stream each) in the throughput run")
     ap.add_argument("--profile-case", action="store_true",
                     help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
     args = ap.parse_args()
