@@ -833,8 +833,20 @@ def cpu_baseline(ev, g, fm, grid_t, target_s=15.0):
         done += idx.size
         steps += int(r["n_steps"].sum())
         n *= 2
+    # one core, as the paper's serialised CPU comparison (sec. 3.1), on a smaller sample
+    t1, done1, steps1, n1 = 0.0, 0, 0, 8
+    while t1 < min(5.0, target_s / 3) and done1 < seeds.shape[0]:
+        idx = rng.choice(seeds.shape[0], size=min(n1, seeds.shape[0]), replace=False)
+        t0 = time.perf_counter()
+        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=1)
+        t1 += time.perf_counter() - t0
+        done1 += idx.size
+        steps1 += int(r["n_steps"].sum())
+        n1 *= 2
     return {"value": done / t, "unit": "seeds/s", "cores": cores, "kind": "oracle",
             "rkn_steps_per_s": steps / t,
+            "one_core": {"value": done1 / t1, "unit": "seeds/s", "rkn_steps_per_s": steps1 / t1,
+                         "sample": f"{done1} seeds, {t1:.1f} s, one thread"},
             "sample": f"{done} seeds drawn at random from the step's 10^6-seed coarse grid, same event and "
                       f"parameters, {t:.1f} s"}
 
