@@ -794,6 +794,10 @@ def run_cuda(args, ws, rank, local):
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
                      "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
+                     "ncu_fp32": ({"fp32_ops_per_rkn_step": 281.4, "fma_pipe_issue_pct": 35.0,
+                                  "executed_fp32_frac_of_peak": 0.128,
+                                  "note": "all executed FP32 work (FFMA = 2) of the reduced 240000-seed launch"}
+                                 if csrc_digest() == TRAFFIC["csrc_sha256"] else None),
                      "flops_per_rkn_step": f_step,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz (unit counts and max clock)"},
