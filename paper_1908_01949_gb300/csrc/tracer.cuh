@@ -44,10 +44,36 @@ struct FoundList {
     float r2[CDC_MAX_FOUND];
 };
 
-// Visits the fired wires in the search window (half widths band [mm] in
-// radius and d_win <= TAB_BAND [mm] along the layer) around (rho, phi, z):
-// fn(wire, drift, cosa).  The layer's fired bits of the window's cells come
-// from one 64-bit read; only fired wires touch the drift table.
+// Fired cells of layer L in the search window (half widths band [mm] in
+// radius, given as the squared bounds blo2..bhi2, and d_win <= TAB_BAND [mm]
+// along the layer) around (phi, z): bit b of m = cell s0 + b (mod N), from one
+// 64-bit read of the layer's fired bits.  False if the window misses the layer.
+__device__ __forceinline__ bool layer_cells(const DevLayer& L, const uint32_t* fired, float blo2, float bhi2, float z,
+                                            float z2, float phi, float d_win, int& s0, uint32_t& m) {
+    const float rl2 = fmaf(z2, L.tan2a, L.R2);
+    if (rl2 > bhi2 || rl2 < blo2) return false;
+    const float zt = z * L.tana_over_R, zt2 = zt * zt;
+    // stereo twist atan(z tan(a) / R) by its Taylor series (|zt| < 0.2)
+    const float tw = zt * fmaf(zt2, fmaf(zt2, fmaf(zt2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
+    const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
+    if (!(fabsf(c) < 1.0e6f)) return false;  // non-finite state: nothing to look up
+    const float w = d_win * L.cells_per_mm;
+    const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
+    if (i1 < i0) return false;
+    s0 = i0;  // |c| stays near N/2 at most: a few wraps at worst
+    while (s0 < 0) s0 += L.N;
+    while (s0 >= L.N) s0 -= L.N;
+    const uint32_t* fw = fired + L.bword + (s0 >> 5);
+    const unsigned long long pair = ((unsigned long long)__ldg(fw + 1) << 32) | __ldg(fw);
+    // the geometry keeps i1 - i0 <= 31 (window of at most 32 cells)
+    m = (uint32_t)(pair >> (s0 & 31)) & (0xffffffffu >> (31 - min(i1 - i0, 31)));
+    return true;
+}
+
+// Visits the fired wires in the search window around (rho, phi, z), layer by
+// layer and cell by cell: fn(wire, drift, cosa).  Only fired wires touch the
+// drift table.  The per-layer arithmetic is that of layer_cells, written out
+// here: the stepping loop's register allocation is better that way.
 template <class Fn>
 __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2* s_tab, const float* dtab,
                                              const uint32_t* fired, float max_drift, float band, float d_win,
@@ -61,19 +87,17 @@ __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2
         const float rl2 = fmaf(z2, L.tan2a, L.R2);
         if (rl2 > bhi2 || rl2 < blo2) continue;
         const float zt = z * L.tana_over_R, zt2 = zt * zt;
-        // stereo twist atan(z tan(a) / R) by its Taylor series (|zt| < 0.2)
         const float tw = zt * fmaf(zt2, fmaf(zt2, fmaf(zt2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
         const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
-        if (!(fabsf(c) < 1.0e6f)) continue;  // non-finite state: nothing to look up
+        if (!(fabsf(c) < 1.0e6f)) continue;
         const float w = d_win * L.cells_per_mm;
         const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
         if (i1 < i0) continue;
-        int s0 = i0;  // |c| stays near N/2 at most: a few wraps at worst
+        int s0 = i0;
         while (s0 < 0) s0 += L.N;
         while (s0 >= L.N) s0 -= L.N;
         const uint32_t* fw = fired + L.bword + (s0 >> 5);
         const unsigned long long pair = ((unsigned long long)__ldg(fw + 1) << 32) | __ldg(fw);
-        // the geometry keeps i1 - i0 <= 31 (window of at most 32 cells)
         uint32_t m = (uint32_t)(pair >> (s0 & 31)) & (0xffffffffu >> (31 - min(i1 - i0, 31)));
         while (m) {
             const int b = __ffs(m) - 1;

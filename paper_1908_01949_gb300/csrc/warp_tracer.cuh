@@ -6,8 +6,9 @@
 //     the RKN chain runs without divergence;
 //   - the candidate list holds one wire per lane and its sign tests run in
 //     parallel;
-//   - a window search hands one fired wire to each lane (layer by layer, cell
-//     by cell, the visiting order of visit_window);
+//   - a window search takes one layer per lane, places the layers' fired
+//     wires by a warp prefix sum in the visiting order of visit_window (layer
+//     by layer, cell by cell) and hands one wire to each lane;
 //   - the record of wires scored below lambda lives in shared memory, where
 //     all lanes search it at once.
 // Minima are recorded in the same order as by Tracer, so both compute the
@@ -20,53 +21,87 @@ namespace cdc {
 
 constexpr unsigned WARP_ALL = 0xffffffffu;
 constexpr int WARP_LIST_CAP = 32;  // candidate wires per seed: one per lane
+constexpr int WIN_CAP = 128;       // fired wires of one window kept in shared memory
 
-// Record of one warp's seed: wire | partition << 16, and res^2.
+// Per-warp shared memory: the record of the warp's seed (wire | partition <<
+// 16, and res^2) and the fired wires of the current window (wire | layer << 16).
 struct WarpFound {
     uint32_t key[CDC_MAX_FOUND];
     float r2[CDC_MAX_FOUND];
+    uint32_t win[WIN_CAP];
 };
 
 // Fired wire number j of the search window around (rho, phi, z), counted in
-// the visiting order of visit_window, as (wire, cosa), or wire = -1.  Returns
-// the number of fired wires in the window.  All arguments but j are the same
-// on every lane, so the layer loop does not diverge.
-__device__ __forceinline__ int window_nth(const DevLayer* s_lay, const uchar2* s_tab, const uint32_t* fired,
-                                          float band, float d_win, float rho, float phi, float z, int j, int& wire,
-                                          float& cosa) {
+// the visiting order of visit_window, as (wire, cosa), or wire = -1; serial
+// over the layers (all arguments but j equal on every lane).  Serves windows
+// with more than WIN_CAP fired wires.
+__device__ __forceinline__ void window_nth(const DevLayer* s_lay, const uchar2* s_tab, const uint32_t* fired,
+                                           float band, float d_win, float rho, float phi, float z, int j, int& wire,
+                                           float& cosa) {
     wire = -1;
     cosa = 1.f;
     const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
-    if (lr.x > lr.y) return 0;
+    if (lr.x > lr.y) return;
     const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
     const float blo2 = blo * blo, bhi2 = bhi * bhi, z2 = z * z;
     int total = 0;
     for (int l = lr.x; l <= lr.y; ++l) {
         const DevLayer& L = s_lay[l];
-        const float rl2 = fmaf(z2, L.tan2a, L.R2);
-        if (rl2 > bhi2 || rl2 < blo2) continue;
-        const float zt = z * L.tana_over_R, zt2 = zt * zt;
-        const float tw = zt * fmaf(zt2, fmaf(zt2, fmaf(zt2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
-        const float c = (phi - tw - L.phi_off) * L.n_over_2pi;
-        if (!(fabsf(c) < 1.0e6f)) continue;
-        const float w = d_win * L.cells_per_mm;
-        const int i0 = (int)ceilf(c - w), i1 = (int)floorf(c + w);
-        if (i1 < i0) continue;
-        int s0 = i0;
-        while (s0 < 0) s0 += L.N;
-        while (s0 >= L.N) s0 -= L.N;
-        const uint32_t* fw = fired + L.bword + (s0 >> 5);
-        const unsigned long long pair = ((unsigned long long)__ldg(fw + 1) << 32) | __ldg(fw);
-        const uint32_t m = (uint32_t)(pair >> (s0 & 31)) & (0xffffffffu >> (31 - min(i1 - i0, 31)));
+        int s0;
+        uint32_t m;
+        if (!layer_cells(L, fired, blo2, bhi2, z, z2, phi, d_win, s0, m)) continue;
         const int cnt = __popc(m);
         if (j >= total && j < total + cnt) {
             int ii = s0 + (int)__fns(m, 0, j - total + 1);
             if (ii >= L.N) ii -= L.N;
             wire = L.base + ii;
             cosa = L.cosa;
+            return;
         }
         total += cnt;
     }
+}
+
+// The fired wires of the search window around (rho, phi, z) in the visiting
+// order of visit_window, written to win[0, min(total, WIN_CAP)) as wire |
+// layer << 16; returns their number.  Lane k takes layer lr.x + k (+ 32 per
+// chunk of layers) and a warp prefix sum of the per-layer counts places its
+// wires.  Called by all lanes with equal arguments.
+__device__ __forceinline__ int window_gather(const DevLayer* s_lay, const uchar2* s_tab, const uint32_t* fired,
+                                             float band, float d_win, float rho, float phi, float z, int lane,
+                                             uint32_t* win) {
+    const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
+    if (lr.x > lr.y) return 0;
+    const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
+    const float blo2 = blo * blo, bhi2 = bhi * bhi, z2 = z * z;
+    int total = 0;
+    __syncwarp();  // the previous window's readers are done
+    for (int l0 = lr.x; l0 <= lr.y; l0 += 32) {
+        const int l = l0 + lane;
+        int s0 = 0;
+        uint32_t m = 0u;
+        if (l <= lr.y && !layer_cells(s_lay[l], fired, blo2, bhi2, z, z2, phi, d_win, s0, m)) m = 0u;
+        const int cnt = __popc(m);
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(WARP_ALL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (m) {
+            const DevLayer& L = s_lay[l];
+            int pos = total + inc - cnt;
+            do {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                int ii = s0 + b;
+                if (ii >= L.N) ii -= L.N;
+                if (pos < WIN_CAP) win[pos] = (uint32_t)(L.base + ii) | ((uint32_t)l << 16);
+                ++pos;
+            } while (m);
+        }
+        total += __shfl_sync(WARP_ALL, inc, 31);
+    }
+    __syncwarp();
     return total;
 }
 
@@ -77,12 +112,29 @@ struct WarpTracer {
     const float* dtab;
     const uint32_t* fired;
     WarpFound* rec;
-    int c_wire;  // this lane's candidate (lanes below nc): wire, slope g, drift, cosa
+    int c_wire;  // this lane's candidate (lanes below nc): wire, its geometry, slope g, drift, cosa
+    float4 c_W;
     float c_g, c_d, c_cosa;
     int n, part, nf, nc, lane;
     bool outside, over;
     float eacc;
     uint32_t flags;
+
+    // Entry j of the window gathered into rec->win (tot wires): (wire, cosa),
+    // or wire = -1 past the end.
+    __device__ __forceinline__ void window_entry(const DevLayer* s_lay, const uchar2* s_tab, float band, float d_win,
+                                                 float rho, float phi, float z, int tot, int j, int& wire,
+                                                 float& cosa) const {
+        wire = -1;
+        cosa = 1.f;
+        if (j < min(tot, WIN_CAP)) {
+            const uint32_t k = rec->win[j];
+            wire = (int)(k & 0xffffu);
+            cosa = s_lay[k >> 16].cosa;
+        } else if (j < tot) {
+            window_nth(s_lay, s_tab, fired, band, d_win, rho, phi, z, j, wire, cosa);
+        }
+    }
 
     // Best squared residual of `wire` below lambda (arguments equal on all
     // lanes); Eq. 1 accumulates min(res^2, lambda) - lambda on top of H lambda.
@@ -143,11 +195,12 @@ struct WarpTracer {
         const float kap = fabsf(s.lam) * P.b_max;
         const float bend = fmaf(0.5f * kap, reach * reach, 0.01f);
         const float phi = atan2f(y, x);
-        for (int pass = 0;; ++pass) {
+        const float band = P.band + wide, d_win = P.d_win + wide;
+        const int tot = window_gather(s_lay, s_tab, fired, band, d_win, rho, phi, z, lane, rec->win);
+        for (int pass = 0; pass * 32 < tot; ++pass) {
             int wire;
             float cosa;
-            const int tot = window_nth(s_lay, s_tab, fired, P.band + wide, P.d_win + wide, rho, phi, z,
-                                       pass * 32 + lane, wire, cosa);
+            window_entry(s_lay, s_tab, band, d_win, rho, phi, z, tot, pass * 32 + lane, wire, cosa);
             bool keep = false;
             float g = 0.f, d = 0.f;
             if (wire >= 0) {
@@ -181,8 +234,8 @@ struct WarpTracer {
             }
             if (nc + nk > WARP_LIST_CAP) over = true;
             nc = min(nc + nk, WARP_LIST_CAP);
-            if (tot <= (pass + 1) * 32) break;
         }
+        if (lane < nc) c_W = __ldg(G.wires + c_wire);
     }
 
     // Seed state, the start-of-track minima and the first candidate list.
@@ -202,17 +255,18 @@ struct WarpTracer {
         eacc = 0.f;
         flags = 0u;
         c_wire = 0;
+        c_W = make_float4(0.f, 0.f, 0.f, 0.f);
         c_g = c_d = 0.f;
         c_cosa = 1.f;
         const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
         const float rho = rho_of(x, y);
         if (in_chamber(s_tab, rho)) {
             const float phi = atan2f(y, x);
-            for (int pass = 0;; ++pass) {
+            const int tot = window_gather(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, z, lane, rec->win);
+            for (int pass = 0; pass * 32 < tot; ++pass) {
                 int wire;
                 float cosa;
-                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, z, pass * 32 + lane, wire,
-                                           cosa);
+                window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, z, tot, pass * 32 + lane, wire, cosa);
                 float r2 = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
@@ -226,7 +280,6 @@ struct WarpTracer {
                     }
                 }
                 record_lanes(P, r2, wire, 0);
-                if (tot <= (pass + 1) * 32) break;
             }
         }
         rebuild(G, P, s_lay, s_tab);
@@ -248,7 +301,7 @@ struct WarpTracer {
         if (over) return;
         float r2 = INFINITY;
         if (lane < nc) {
-            const float4 W = __ldg(G.wires + c_wire);
+            const float4 W = c_W;
             float tp2;
             const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, c_cosa, tp2);
             if (c_g < 0.f && g1 >= 0.f)
@@ -268,11 +321,11 @@ struct WarpTracer {
         if (over && in_chamber(s_tab, rho)) {
             const float kap = fabsf(s.lam) * P.b_max;
             const float phi = atan2f(ny, nx);
-            for (int pass = 0;; ++pass) {
+            const int tot = window_gather(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, lane, rec->win);
+            for (int pass = 0; pass * 32 < tot; ++pass) {
                 int wire;
                 float cosa;
-                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, pass * 32 + lane,
-                                           wire, cosa);
+                window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, nz, tot, pass * 32 + lane, wire, cosa);
                 float r2 = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
@@ -289,7 +342,6 @@ struct WarpTracer {
                     }
                 }
                 record_lanes(P, r2, wire, part);
-                if (tot <= (pass + 1) * 32) break;
             }
         }
         const bool now_out = rho >= G.R0;
@@ -306,11 +358,11 @@ struct WarpTracer {
         }
         if (stop && part < P.max_part && in_chamber(s_tab, rho)) {
             const float phi = atan2f(ny, nx);
-            for (int pass = 0;; ++pass) {
+            const int tot = window_gather(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, lane, rec->win);
+            for (int pass = 0; pass * 32 < tot; ++pass) {
                 int wire;
                 float cosa;
-                const int tot = window_nth(s_lay, s_tab, fired, P.band, P.d_win, rho, phi, nz, pass * 32 + lane,
-                                           wire, cosa);
+                window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, nz, tot, pass * 32 + lane, wire, cosa);
                 float r2 = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
@@ -324,7 +376,6 @@ struct WarpTracer {
                     }
                 }
                 record_lanes(P, r2, wire, part);
-                if (tot <= (pass + 1) * 32) break;
             }
         }
         return !stop;
