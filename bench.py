@@ -58,7 +58,10 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
 # single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
 # kernel sources it was taken on (SHA-256 over the csrc files), else reported as null.
-TRAFFIC = {"bytes": 33_518_848 + 14_779_648, "csrc_sha256": "3557ed93e59559aa08b88eaaf81fc8fefaea1ed48c849dfd2348e30933545fbb"}
+TRAFFIC = {"bytes": 33_329_408 + 14_821_632, "csrc_sha256": "b3f2f472583ca1f1c1faf134d947d91325f9d1253472c9122c62e4769f5566e0"}
+# Executed FP32 work of the coarse-round launch (ncu, reduced 240000-seed case), same validity rule.
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "fma_pipe_issue_pct": 35.0, "executed_fp32_frac_of_peak": 0.128,
+               "csrc_sha256": "3557ed93e59559aa08b88eaaf81fc8fefaea1ed48c849dfd2348e30933545fbb"}
 
 
 def csrc_digest() -> str:
@@ -664,8 +667,14 @@ def run_cuda(args, ws, rank, local):
         tune_ms = None
     else:
         tuned, tune_ms = tr.tune(off, wid, dr, grid, sp, reps=3, stream=stream)
+    # zoom rounds (972 seeds per event): one event at a time, one warp per seed
+    # shortens them (latency); with many events in flight one lane per seed
+    # leaves the other events' coarse rounds the warp slots (throughput)
+    lat_ws = args.warp_seeds if args.warp_seeds is not None else ctx.cdc_get_scan_config()[2]
+    thr_ws = args.stream_warp_seeds
     for q in slots:
-        q["ctx"].cdc_set_scan_config(*tuned)
+        q["ctx"].cdc_set_scan_config(*tuned, thr_ws)
+    ctx.cdc_set_scan_config(*tuned, lat_ws)
     launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan clear+stage, 5/round, 9 zoom grids, assign
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     for i in range(args.warmup * n_in):
@@ -688,6 +697,7 @@ def run_cuda(args, ws, rank, local):
         lat_ms.append(e0.elapsed_time(e1))
     ktot, kn, kper = ctx.cdc_kernel_time()
     ctx.cdc_kernel_timer(False)
+    ctx.cdc_set_scan_config(*tuned, thr_ws)
     rkn = q0["steps"].cpu().numpy().astype(np.float64)
     coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
     coarse_steps = float(rkn[0]) / args.steps
@@ -773,6 +783,8 @@ def run_cuda(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "seeds_per_step": seeds_per_step, "events_per_step": 1,
                    "events_in_flight": n_in,
+                   "zoom_rounds": {"throughput_run": "warp per seed" if thr_ws >= N_ZOOM * 243 else "lane per seed",
+                                   "latency_run": "warp per seed" if lat_ws >= N_ZOOM * 243 else "lane per seed"},
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"event-parallel x{ws} (independent events per GPU, no collective)"},
         "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
@@ -794,10 +806,9 @@ def run_cuda(args, ws, rank, local):
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
                      "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
-                     "ncu_fp32": ({"fp32_ops_per_rkn_step": 281.4, "fma_pipe_issue_pct": 35.0,
-                                  "executed_fp32_frac_of_peak": 0.128,
-                                  "note": "all executed FP32 work (FFMA = 2) of the reduced 240000-seed launch"}
-                                 if csrc_digest() == TRAFFIC["csrc_sha256"] else None),
+                     "ncu_fp32": (dict({k: v for k, v in FP32_COUNTS.items() if k != "csrc_sha256"},
+                                       note="all executed FP32 work (FFMA = 2) of the reduced 240000-seed launch")
+                                  if csrc_digest() == FP32_COUNTS["csrc_sha256"] else None),
                      "flops_per_rkn_step": f_step,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz (unit counts and max clock)"},
@@ -900,7 +911,7 @@ def run_reference(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-oracle baseline sample")
@@ -922,7 +933,12 @@ def main():
     ap.add_argument("--bidir-events", type=int, default=32, help="events of the bidirectional leg")
     ap.add_argument("--scan-shape", default=None,
                     help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")
-    ap.add_argument("--inflight", type=int, default=3,
+    ap.add_argument("--warp-seeds", type=int, default=None,
+                    help="latency run: zoom rounds with at most this many seeds run one warp per seed (0: never; "
+                         "default: the library's, 16 per SM)")
+    ap.add_argument("--stream-warp-seeds", type=int, default=0,
+                    help="the same for the throughput and end-to-end runs (default 0: one lane per seed)")
+    ap.add_argument("--inflight", type=int, default=8,
                     help="events in flight (one context and stream each) in the throughput run")
     ap.add_argument("--profile-case", action="store_true",
                     help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
