@@ -101,6 +101,16 @@ __device__ __forceinline__ void field_apply(float4 cz, float4 cr, float u, float
     by = s * y;
 }
 
+// The two coefficient sets of one cell: 32 contiguous bytes on a 32-byte
+// boundary (the table is one allocation of 32-byte records), read by one
+// 256-bit load through the read-only path.  Each lane of a warp usually reads
+// a different cell, so one load instead of two halves the cache wavefronts.
+__device__ __forceinline__ void load_cell(const float4* c, float4& cz, float4& cr) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(cz.x), "=f"(cz.y), "=f"(cz.z), "=f"(cz.w), "=f"(cr.x), "=f"(cr.y), "=f"(cr.z), "=f"(cr.w)
+        : "l"(c));
+}
+
 template <int KIND>
 __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, float z, float& bx, float& by,
                                            float& bz) {
@@ -110,8 +120,9 @@ __device__ __forceinline__ void field_eval(const DevField& F, float x, float y, 
         bz = F.B0;
     } else {
         float u, v, rinv;
-        const float4* c = F.cells + 2 * field_cell(F, x, y, z, u, v, rinv);
-        field_apply(__ldg(c), __ldg(c + 1), u, v, rinv, x, y, bx, by, bz);
+        float4 cz, cr;
+        load_cell(F.cells + 2 * field_cell(F, x, y, z, u, v, rinv), cz, cr);
+        field_apply(cz, cr, u, v, rinv, x, y, bx, by, bz);
     }
 }
 
