@@ -58,7 +58,7 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
 # single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
 # kernel sources it was taken on (SHA-256 over the csrc files), else reported as null.
-TRAFFIC = {"bytes": 33_329_408 + 14_821_632, "csrc_sha256": "b3f2f472583ca1f1c1faf134d947d91325f9d1253472c9122c62e4769f5566e0"}
+TRAFFIC = {"bytes": 33_485_824 + 14_628_352, "csrc_sha256": "46af1ff2d25c83c89e0b6c599f244e38149c50d18eafce31dc16dd1045b28c8d"}
 # Executed FP32 work of the coarse-round launch (ncu, reduced 240000-seed case), same validity rule.
 FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "executed_fp32_frac_of_peak": 0.131,
                "csrc_sha256": "46af1ff2d25c83c89e0b6c599f244e38149c50d18eafce31dc16dd1045b28c8d"}
