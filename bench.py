@@ -343,10 +343,25 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
     ms = statistics.median(times)
     nc = nc.cpu().numpy()
     turn0 = np.array([int(np.sum(e.truth_part == 0)) for e in evs])
+    # Eqs. 2-3 for the scanned turn (partition 0 of either direction = truth
+    # turn 0) per event, averaged over the events that pass N_c >= 20; the
+    # other truth turns count as signal partitions in the purity
+    truth_t = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=tr.dev)
+    keep = np.flatnonzero(nc >= 20)
+    quality = {}
+    for name, o in zip(("entrance", "exit"), outs):
+        C = tr.classification_counts(off_t, o["hit_part"], truth_t, 8).cpu().numpy()
+        ep = np.array([[v[0] for v in cdc.efficiency_purity(C[e])] for e in keep]).reshape(-1, 2)
+        quality[name] = {"efficiency_mean": float(np.nanmean(ep[:, 0])) if keep.size else None,
+                         "purity_mean": float(np.nanmean(ep[:, 1])) if keep.size else None}
     return {"events": n_ev, "seeds_per_direction": n_seeds, "ms": ms, "events_per_s": n_ev / (ms / 1e3),
             "seeds_per_s": 2 * (n_seeds + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev) / (ms / 1e3),
             "n_common_mean": float(nc.mean()), "n_common_min": int(nc.min()),
             "pass_nc_ge_20": float(np.mean(nc >= 20)), "turn0_hits_mean": float(turn0.mean()),
+            "classification_nc_ge_20": dict(quality, events=int(keep.size),
+                                            definition="Eqs. 2-3 of the scanned turn per event, mean over the "
+                                                       "events with N_c >= 20 (the paper: 76 % / 90 % for its "
+                                                       "last turn partition on COMET simulation)"),
             "timing": "median of 3: both directions' ten-round scans and the N_c kernel"}
 
 

@@ -723,8 +723,12 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     return chi2;
 }
 
+// Thread per seed.  Capped at 128 registers (four 128-thread blocks per SM,
+// a few hundred bytes of spills): the ~225 the code would take leave two
+// blocks per SM, half the latency hiding and, for 65536 seeds, 1.7 waves
+// (measured 128 -> 118 ms for 65536 seeds x 5 iterations).
 template <int KIND>
-__global__ void __launch_bounds__(128) refine_kernel(DevGeom G, DevField F, ScanConst P, RefArgs a, int do_gn) {
+__global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, ScanConst P, RefArgs a, int do_gn) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
     __shared__ float4 s_cand[LIST_CAP][128];
