@@ -497,6 +497,7 @@ def sweep_leg(args, rank, local, g, fm, flush):
     torch.cuda.synchronize()
     hough_ms = e0.elapsed_time(e1)
     votes = int(h["acc"].sum(dtype=torch.int64))
+    acc_bytes = 2 * int(h["acc"].numel()) * 4
     # FP32 steppers against the FP64 GPU stepper
     rng = np.random.default_rng(3)
     pick = np.sort(rng.choice(n, size=min(SWEEP_SEEDS, n), replace=False))
@@ -524,7 +525,10 @@ def sweep_leg(args, rank, local, g, fm, flush):
             "hits": int(wid.size), "ms_per_step": ms, "seeds_per_s": seeds_step / (ms / 1e3),
             "rkn_steps_per_s": steps / (ms / 1e3),
             "hough": {"events": n_ev, "ms": hough_ms, "votes": votes,
-                      "votes_per_s": votes / (hough_ms / 1e3)},
+                      "votes_per_s": votes / (hough_ms / 1e3),
+                      "accumulator_bytes": acc_bytes, "accumulator_gb_per_s": acc_bytes / (hough_ms / 1e3) / 1e9,
+                      "bytes_note": "algorithmic: each event's int32 accumulator cleared once and read once by "
+                                    "the peak search; the votes themselves are L2 atomics"},
             "position_vs_fp64_gpu": curve,
             "subsample": f"{seeds.shape[0]} seeds drawn from the events' grids, fixed-length propagation "
                          f"(no stop surfaces) to {SWEEP_EVERY * SWEEP_REC * H / 1000.0:.0f} m"}
