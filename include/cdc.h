@@ -257,7 +257,7 @@ int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* pe
 /* ---- launch shape of the seed scan and its autotuner -------------------- */
 
 /* Launch shape of the seed scan (no counterpart in the paper, which launches
- * one block per seed, sec. 3).  block = threads, i.e. seeds in flight, per
+ * one block per seed, sec. 2.2).  block = threads, i.e. seeds in flight, per
  * block of the one-lane-per-seed kernel (128 or 256); chunk = RKN steps a lane
  * takes between seed refills (16 or 32); warp_seeds = zoom rounds with at most
  * this many seeds (n_events * n_zoom * 243) run one warp per seed instead,
@@ -303,7 +303,7 @@ int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int3
 int cdc_reserve_split(cdc_ctx* ctx, int chunk, int max_steps);
 
 /* The coarse scan organised as in the paper's "kernel function separation"
- * (sec. 3): for `chunk` seeds at a time, kernel A (one thread per seed) records
+ * (sec. 4.2): for `chunk` seeds at a time, kernel A (one thread per seed) records
  * the state after every RKN step to the end of the track, then kernel B (one
  * block per seed, threads over the event's hits: the block-per-seed,
  * thread-per-wire layout of sec. 2.2) finds every hit's distance of closest

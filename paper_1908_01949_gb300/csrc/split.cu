@@ -1,4 +1,4 @@
-// The paper's two-kernel organisation of the scan (arXiv:1908.01949 sec. 3,
+// The paper's two-kernel organisation of the scan (arXiv:1908.01949 sec. 4.2,
 // "kernel function separation"), kept as an A/B reference for the fused scan:
 //   A. one thread per seed propagates the seed to the end of its track and
 //      records the state after every RKN step;
