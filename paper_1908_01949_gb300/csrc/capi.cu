@@ -491,6 +491,7 @@ int cdc_scan_seeds_split(cdc_ctx* c, int n_events, int64_t n_seeds, const int32_
     if (!c->geom || !c->field) return fail(c, CDC_ERR_NOT_LOADED, "geometry or field not loaded");
     if (n_events < 0 || n_seeds < 0) return fail(c, CDC_ERR_ARG, "n_events or n_seeds < 0");
     if (n_events == 0) return CDC_OK;
+    if (!p) return fail(c, CDC_ERR_ARG, "scan params is NULL");
     cdc_scan_params p1 = *p;
     p1.n_rounds = 1;
     int rc = check_scan_params(c, &p1, true);

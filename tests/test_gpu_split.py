@@ -44,3 +44,28 @@ def test_split_scan_equals_fused_scan_and_oracle(case, field_map):
     ref = O.scan(g, f, ev.wire_id, ev.drift.astype(np.float64), O.grid_values(grid), oracle_params(p))
     bad, excluded, worst = compare_scores(Es, ref)
     assert bad.size == 0, (bad[:10], worst)
+
+
+def test_split_scan_argument_errors():
+    """Missing parameters, a missing split workspace and a step limit above
+    the reserved one are status codes, not crashes."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, grid = S.cfg1_case(3)
+    n = int(np.prod(grid["n"][0]))
+    tr = tracker(g, f, max_seeds=n)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    gt = cdc.grids_to_tensor(grid, tr.dev)
+    E = torch.empty(n, dtype=torch.float32, device=tr.dev)
+    flags = torch.empty(1, dtype=torch.int32, device=tr.dev)
+    ptr = [t.data_ptr() for t in (off, wid, dr, gt, E, flags)]
+    L = tr.ctx.L
+    assert L.cdc_scan_seeds_split(tr.ctx.h, 1, n, ptr[0], ptr[1], ptr[2], ptr[3], None, ptr[4], ptr[5], None) == -1
+    p = cdc.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1, k=8, n_rounds=1)
+    with pytest.raises(cdc.CdcError):                      # no split workspace reserved yet
+        tr.ctx.cdc_scan_seeds_split(1, n, off, wid, dr, gt, p, E, flags)
+    tr.ctx.cdc_reserve_split(1000, 500)
+    with pytest.raises(cdc.CdcError):                      # max_steps above the reserve
+        tr.ctx.cdc_scan_seeds_split(1, n, off, wid, dr, gt, p, E, flags)
+    with pytest.raises(cdc.CdcError):
+        tr.ctx.cdc_reserve_split(0, 500)
