@@ -102,6 +102,7 @@ void free_workspace(Workspace& W) {
     dfree(W.round_keys);
     dfree(W.best_keys);
     dfree(W.zgrids);
+    dfree(W.perm);
     W = Workspace{};
 }
 
@@ -365,7 +366,8 @@ int cdc_reserve(cdc_ctx* c, int max_events, int64_t max_seeds, int64_t max_hits)
         (e = dalloc(W.seg_keys, (size_t)W.seg_cap * CDC_MAX_K)) != cudaSuccess ||
         (e = dalloc(W.round_keys, (size_t)2 * max_events * CDC_MAX_K)) != cudaSuccess ||
         (e = dalloc(W.best_keys, (size_t)max_events * CDC_MAX_K)) != cudaSuccess ||
-        (e = dalloc(W.zgrids, (size_t)2 * max_events * CDC_MAX_ZOOM)) != cudaSuccess) {
+        (e = dalloc(W.zgrids, (size_t)2 * max_events * CDC_MAX_ZOOM)) != cudaSuccess ||
+        (e = dalloc(W.perm, (size_t)max_events * PERM_CAP)) != cudaSuccess) {
         free_workspace(W);
         return fail(c, CDC_ERR_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
     }

@@ -287,11 +287,15 @@ __device__ __forceinline__ void grid_seed(const cdc_grid& g, long long idx, floa
     for (int a = 0; a < 5; ++a) out[a] = fmaf((float)ia[a] - 0.5f * (float)(g.n[a] - 1), g.step[a], g.centre[a]);
 }
 
+constexpr int PERM_CAP = 4096;  // (z0, pz0) blocks of a coarse grid that can be reordered
+
 // Row-major index of the q-th seed of a grid in scan order: (z0, pz0)
 // outermost, then theta0, px0, py0, so that consecutive seeds (the lanes of a
 // warp) differ by a step of a transverse parameter, follow nearly the same
-// path and visit nearly the same wires.
-__device__ __forceinline__ long long scan_order_index(const cdc_grid& g, long long q) {
+// path and visit nearly the same wires.  The (z0, pz0) blocks come in the
+// order perm gives (perm[b] = iz * n_pz0 + ip of the b-th block), or in their
+// natural order for perm == nullptr or grids of more than PERM_CAP blocks.
+__device__ __forceinline__ long long scan_order_index(const cdc_grid& g, long long q, const uint16_t* perm) {
     const int nt = g.n[0], nz = g.n[1], nx = g.n[2], ny = g.n[3], np = g.n[4];
     const long long iy = q % ny;
     q /= ny;
@@ -299,6 +303,7 @@ __device__ __forceinline__ long long scan_order_index(const cdc_grid& g, long lo
     q /= nx;
     const long long it = q % nt;
     q /= nt;
+    if (perm && (long long)nz * np <= PERM_CAP) q = perm[q];
     const long long ip = q % np;
     const long long iz = q / np;
     return (((it * nz + iz) * nx + ix) * ny + iy) * np + ip;
@@ -331,15 +336,16 @@ __device__ __forceinline__ int find_event(const long long* off, int n, long long
 }
 
 // The q-th seed of event e in scan order (scan_order_index within each of the
-// event's grids): its values, and its row-major index among the event's seeds.
+// event's grids; perm: the block order of a single grid, or nullptr): its
+// values, and its row-major index among the event's seeds.
 __device__ __forceinline__ long long event_seed_ordered(const cdc_grid* grids, int gpe, int e, long long q,
-                                                       float* sd) {
+                                                       float* sd, const uint16_t* perm) {
     long long base = 0;
     for (int g = 0; g < gpe; ++g) {
         const cdc_grid& gr = grids[(size_t)e * gpe + g];
         const long long c = grid_count(gr);
         if (q < c || g == gpe - 1) {
-            const long long li = scan_order_index(gr, q);
+            const long long li = scan_order_index(gr, q, gpe == 1 ? perm : nullptr);
             grid_seed(gr, li, sd);
             return base + li;
         }

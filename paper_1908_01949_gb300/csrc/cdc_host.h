@@ -18,6 +18,7 @@ struct Workspace {
     uint64_t* round_keys = nullptr;        // [2][max_events][CDC_MAX_K]
     uint64_t* best_keys = nullptr;         // [max_events][CDC_MAX_K]
     cdc_grid* zgrids = nullptr;            // [2][max_events][CDC_MAX_ZOOM]
+    uint16_t* perm = nullptr;              // [max_events][PERM_CAP]: coarse-grid block order (nullptr: natural)
     int max_events = 0;
     long long e_cap = 0, seg_cap = 0;
     int n_wires = 0;

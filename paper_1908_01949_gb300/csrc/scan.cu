@@ -148,7 +148,50 @@ struct ScanIO {
     float* E;
     uint32_t* flags;
     unsigned long long* steps;
+    const uint16_t* perm;  // [n_events][PERM_CAP] block order of single-grid rounds, or nullptr
 };
+
+// Per event, the (z0, pz0) blocks of its coarse grid in the order the scan
+// takes them: longest estimated track first, so that the persistent scan ends
+// on short tracks and its warps run out of work together.  Estimate: the path
+// to the end plate the track heads for, (z_half - z0 sgn(pz dir)) p / |pz|,
+// capped at max_part turns of 2 pi p / (kappa b_max), with (px, py) at the
+// grid centre.  Only the order in which seeds are processed changes, not their
+// scores or indices.  Rank of block i = number of blocks with a larger key, or
+// an equal key and a lower index (a permutation).
+__global__ void __launch_bounds__(1024) order_blocks_kernel(int n_events, const cdc_grid* __restrict__ grids,
+                                                            float z_half, float b_max, int max_part, int direction,
+                                                            uint16_t* perm) {
+    __shared__ float s_key[PERM_CAP];
+    const int e = blockIdx.x;
+    if (e >= n_events) return;
+    const cdc_grid g = grids[e];
+    const int nz = g.n[1], np = g.n[4];
+    if (nz < 1 || np < 1 || (long long)nz * np > PERM_CAP) return;  // scan_order_index keeps the natural order
+    const int nb = nz * np;
+    const float px = g.centre[2], py = g.centre[3];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const float z0 = fmaf((float)(i / np) - 0.5f * (float)(nz - 1), g.step[1], g.centre[1]);
+        const float pz = fmaf((float)(i % np) - 0.5f * (float)(np - 1), g.step[4], g.centre[4]);
+        const float p = sqrtf(fmaf(px, px, fmaf(py, py, pz * pz)));
+        const float turn = b_max > 0.f ? 6.28318531f * p / (KAPPA * b_max) : INFINITY;
+        const float side = pz * (float)direction >= 0.f ? 1.f : -1.f;
+        const float sz = fabsf(pz) > 0.f ? fmaxf(z_half - side * z0, 0.f) * p / fabsf(pz) : INFINITY;
+        const float key = fminf(sz, (float)max_part * turn);
+        s_key[i] = key == key ? key : 0.f;
+    }
+    __syncthreads();
+    uint16_t* out = perm + (size_t)e * PERM_CAP;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const float k = s_key[i];
+        int rank = 0;
+        for (int j = 0; j < nb; ++j) {
+            const float kj = s_key[j];
+            rank += (kj > k || (kj == k && j < i)) ? 1 : 0;
+        }
+        out[rank] = (uint16_t)i;
+    }
+}
 
 // Persistent thread-per-seed scorer.  A warp takes 32 consecutive seeds in
 // scan order (neighbours in theta0, px0, py0 at equal z0, pz0: nearly the same
@@ -187,7 +230,8 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                 if (s < total) {
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
-                    my = io.seed_off[ev] + event_seed_ordered(io.grids, io.gpe, ev, s - io.seed_off[ev], sd);
+                    my = io.seed_off[ev] + event_seed_ordered(io.grids, io.gpe, ev, s - io.seed_off[ev], sd,
+                                                              io.perm ? io.perm + (size_t)ev * PERM_CAP : nullptr);
                     T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires),
                            &s_cand[0][threadIdx.x], BS, sd, FL);
                 } else {
@@ -756,8 +800,10 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
         const long long cap = (r == 0 && L.E0) ? (1ll << 62) : W.e_cap;
         prologue_kernel<<<1, 1024, 0, st>>>(ne, grids, gpe, cap, W.seg_cap, W.seed_off, W.seg_off, W.counters,
                                             L.flags);
+        if (r == 0 && W.perm)
+            order_blocks_kernel<<<ne, 1024, 0, st>>>(ne, grids, G.z_half, P.b_max, P.max_part, P.direction, W.perm);
         ScanIO io{W.drift_tab, L.hit_off, grids, gpe, W.seed_off, ne, W.counters, E, L.flags,
-                  L.steps ? L.steps + r : nullptr};
+                  L.steps ? L.steps + r : nullptr, r == 0 ? W.perm : nullptr};
         const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
         if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
         // a round of few seeds (host bound: zoom grids of 3^5 seeds) runs one warp per seed
