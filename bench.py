@@ -58,10 +58,11 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
 # single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
 # kernel sources it was taken on (SHA-256 over the csrc files), else reported as null.
-TRAFFIC = {"bytes": 33_485_824 + 14_628_352, "csrc_sha256": "46af1ff2d25c83c89e0b6c599f244e38149c50d18eafce31dc16dd1045b28c8d"}
-# Executed FP32 work of the coarse-round launch (ncu, reduced 240000-seed case), same validity rule.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "executed_fp32_frac_of_peak": 0.131,
-               "csrc_sha256": "46af1ff2d25c83c89e0b6c599f244e38149c50d18eafce31dc16dd1045b28c8d"}
+TRAFFIC = {"bytes": 34_329_088 + 16_625_152, "csrc_sha256": "78e14bdf99dbf22b35d0fa481a573792688b6bce6d56209257437c1c3ed33a81"}
+# Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
+# 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
+# measured launch.
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "csrc_sha256": "78e14bdf99dbf22b35d0fa481a573792688b6bce6d56209257437c1c3ed33a81"}
 
 
 def csrc_digest() -> str:
@@ -761,6 +762,8 @@ def run_cuda(args, ws, rank, local):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     f_step = flops_per_step(1)
     achieved = f_step * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12 if coarse_ms else None
+    executed = (FP32_COUNTS["fp32_ops_per_rkn_step"] * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12
+                if coarse_ms else None)
 
     # end to end: the same stream of events with each step's inputs copied from
     # pinned host memory and its results (best seeds and scores, hit classes,
@@ -825,8 +828,11 @@ def run_cuda(args, ws, rank, local):
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
                      "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
-                     "ncu_fp32": (dict({k: v for k, v in FP32_COUNTS.items() if k != "csrc_sha256"},
-                                       note="all executed FP32 work (FFMA = 2) of the reduced 240000-seed launch")
+                     "ncu_fp32": ({"fp32_ops_per_rkn_step": FP32_COUNTS["fp32_ops_per_rkn_step"],
+                                   "executed_tflops": executed,
+                                   "executed_fp32_frac_of_peak": executed / peak if executed else None,
+                                   "note": "all executed FP32 work (FFMA = 2) per RKN step from ncu, times this "
+                                           "launch's steps over its CUDA-event time"}
                                   if csrc_digest() == FP32_COUNTS["csrc_sha256"] else None),
                      "flops_per_rkn_step": f_step,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
