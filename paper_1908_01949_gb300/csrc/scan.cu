@@ -815,13 +815,21 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
             else
                 scan_warp_kernel<1><<<nb, 128, 0, st>>>(G, F, P, io);
         } else {
-            kern<<<scan_blocks, bs, 0, st>>>(G, F, P, io);
+            // a zoom round has at most round_seeds seeds: one block per 32 of them (one
+            // cohort each, spread over SMs) instead of the full persistent grid, whose idle
+            // blocks would only contend for SM slots with other streams' work
+            const int nb = r == 0 ? scan_blocks
+                                  : (int)std::min<long long>(scan_blocks, std::max<long long>(1, (round_seeds + 31) / 32));
+            kern<<<nb, bs, 0, st>>>(G, F, P, io);
         }
         if (timed) {
             cudaEventRecord(L.timer.ev[*L.timer.used + 1], st);
             *L.timer.used += 2;
         }
-        topk_partial_kernel<<<num_sms * 2, 256, 0, st>>>(E, W.seed_off, W.seg_off, ne, W.counters, P.k, W.seg_keys);
+        // one warp per 4096-seed segment; a zoom round has at most round_seeds / SEG + ne segments
+        const int tb = r == 0 ? num_sms * 2
+                              : (int)std::min<long long>(num_sms * 2, (round_seeds / SEG + ne + 7) / 8);
+        topk_partial_kernel<<<tb, 256, 0, st>>>(E, W.seed_off, W.seg_off, ne, W.counters, P.k, W.seg_keys);
         uint64_t* rk = W.round_keys + (size_t)(r & 1) * W.max_events * CDC_MAX_K;
         topk_merge_kernel<<<blocks_for((long long)ne * 32, 256), 256, 0, st>>>(W.seg_off, ne, P.k, W.seg_keys, rk);
         merge_best_kernel<<<blocks_for(ne, 64), 64, 0, st>>>(ne, P.k, r, rk, grids, gpe, W.best_keys, L.best_E,
