@@ -695,7 +695,9 @@ def run_cuda(args, ws, rank, local):
     for q in slots:
         q["ctx"].cdc_set_scan_config(*tuned, thr_ws)
     ctx.cdc_set_scan_config(*tuned, lat_ws)
-    launches_per_step = 2 + (6 * N_ROUNDS + 2)       # Hough vote+peaks; scan clear+stage, 5/round, 9 zoom grids, assign
+    # Hough vote + peaks; table clear + staging; block order of the coarse grid; per round prologue, scan,
+    # top-K partial + merge, best merge; a zoom grid build per zoom round; hit assignment
+    launches_per_step = 2 + 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     for i in range(args.warmup * n_in):
         step(slots[i % n_in])
