@@ -717,7 +717,7 @@ def run_cuda(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         lat_ms.append(e0.elapsed_time(e1))
-    ktot, kn, kper = ctx.cdc_kernel_time()
+    _, _, kper = ctx.cdc_kernel_time()
     ctx.cdc_kernel_timer(False)
     ctx.cdc_set_scan_config(*tuned, thr_ws)
     rkn = q0["steps"].cpu().numpy().astype(np.float64)
@@ -902,7 +902,7 @@ def run_reference(args, ws, rank, local):
     oracle_build = O.build()
     g, fm, ev = make_workload(0)
     H_ = O.hough_params()
-    _, cand, cen = O.hough(g, H_, ev.wire_id)
+    _, _, cen = O.hough(g, H_, ev.wire_id)
     tmpl = S.cfg2_grid_template()
     if cen.shape[0]:
         tmpl["centre"][0][[0, 2, 3]] = cen[0]
