@@ -199,3 +199,28 @@ def test_propagated_positions_within_tolerance_per_metre(field_map, precision):
                 err = np.linalg.norm(pos[i, r] - st[j, :3])
                 worst = max(worst, err / (j * 2.0 / 1000.0))
         assert worst < (1e-9 if precision == 1 else 1e-4), (precision, worst)
+
+
+def test_grid_with_more_blocks_than_the_order_table_keeps_natural_order():
+    """A grid of 65 x 65 (z0, pz0) blocks (more than the 4096 the block order
+    handles) is scanned in natural order; its scores and top-K still follow
+    the oracle."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, grid = S.cfg1_case(4)
+    grid["n"][0] = (1, 65, 1, 1, 65)
+    grid["step"][0][1] = 4.0
+    grid["step"][0][4] = 0.5
+    n = int(np.prod(grid["n"][0]))
+    tr = tracker(g, f)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    p = cdc.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1, k=8, n_rounds=1)
+    out = tr.scan(off, wid, dr, cdc.grids_to_tensor(grid, tr.dev), p, want_E=True, n_seeds=n)
+    torch.cuda.synchronize()
+    ref = O.scan(g, f, ev.wire_id, ev.drift.astype(np.float64), O.grid_values(grid), oracle_params(p))
+    bad, excluded, worst = compare_scores(out["E"].cpu().numpy(), ref)
+    assert bad.size == 0, (bad[:10], worst)
+    assert excluded < 0.02 * n
+    idx, _ = keys_to_index(out["topk0"][0].cpu().numpy())
+    ok, diff = check_topk(idx, ref["E"], 8)
+    assert ok, diff
