@@ -103,6 +103,9 @@ void free_workspace(Workspace& W) {
     dfree(W.best_keys);
     dfree(W.zgrids);
     dfree(W.perm);
+    dfree(W.recs);
+    dfree(W.rec_count);
+    dfree(W.run_best);
     W = Workspace{};
 }
 
@@ -367,7 +370,10 @@ int cdc_reserve(cdc_ctx* c, int max_events, int64_t max_seeds, int64_t max_hits)
         (e = dalloc(W.round_keys, (size_t)2 * max_events * CDC_MAX_K)) != cudaSuccess ||
         (e = dalloc(W.best_keys, (size_t)max_events * CDC_MAX_K)) != cudaSuccess ||
         (e = dalloc(W.zgrids, (size_t)2 * max_events * CDC_MAX_ZOOM)) != cudaSuccess ||
-        (e = dalloc(W.perm, (size_t)max_events * PERM_CAP)) != cudaSuccess) {
+        (e = dalloc(W.perm, (size_t)max_events * PERM_CAP)) != cudaSuccess ||
+        (e = dalloc(W.recs, (size_t)max_events * REC_SLOTS)) != cudaSuccess ||
+        (e = dalloc(W.rec_count, (size_t)max_events)) != cudaSuccess ||
+        (e = dalloc(W.run_best, (size_t)max_events)) != cudaSuccess) {
         free_workspace(W);
         return fail(c, CDC_ERR_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
     }

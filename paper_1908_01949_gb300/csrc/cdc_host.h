@@ -19,6 +19,9 @@ struct Workspace {
     uint64_t* best_keys = nullptr;         // [max_events][CDC_MAX_K]
     cdc_grid* zgrids = nullptr;            // [2][max_events][CDC_MAX_ZOOM]
     uint16_t* perm = nullptr;              // [max_events][PERM_CAP]: coarse-grid block order (nullptr: natural)
+    SeedRecord* recs = nullptr;            // [max_events][REC_SLOTS]: records of improving zoom-round seeds
+    unsigned* rec_count = nullptr;         // [max_events]: records claimed in this call
+    unsigned* run_best = nullptr;          // [max_events]: the event's best score so far (float bits)
     int max_events = 0;
     long long e_cap = 0, seg_cap = 0;
     int n_wires = 0;

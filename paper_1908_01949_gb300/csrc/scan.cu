@@ -149,7 +149,22 @@ struct ScanIO {
     uint32_t* flags;
     unsigned long long* steps;
     const uint16_t* perm;  // [n_events][PERM_CAP] block order of single-grid rounds, or nullptr
+    SeedRecord* recs;      // [n_events][REC_SLOTS] records of improving seeds (zoom rounds), or nullptr
+    unsigned* rec_count;   // [n_events]
+    unsigned* run_best;    // [n_events] best score so far (float bits)
+    int round;
 };
+
+// A slot for the record of a zoom-round seed whose score is at most its
+// event's best so far (the running minimum starts each round at the best of
+// the previous rounds), or -1: only such a seed can become the event's best.
+__device__ __forceinline__ int record_slot(const ScanIO& io, int ev, float score) {
+    if (!(score >= 0.f)) return -1;
+    const unsigned bits = __float_as_uint(score);  // non-negative floats order as their bits
+    if (bits > atomicMin(io.run_best + ev, bits)) return -1;
+    const unsigned slot = atomicAdd(io.rec_count + ev, 1u);
+    return slot < (unsigned)REC_SLOTS ? (int)slot : -1;
+}
 
 // Per event, the (z0, pz0) blocks of its coarse grid in the order the scan
 // takes them: longest estimated track first, so that the persistent scan ends
@@ -244,7 +259,21 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
             for (int it = 0; it < CHUNK; ++it) {
                 if (!T.step(G, F, P, s_lay, s_tab, FL)) {
                     int H = io.hit_off[ev + 1] - io.hit_off[ev];
-                    io.E[my] = T.score(P, H);
+                    const float score = T.score(P, H);
+                    io.E[my] = score;
+                    if (io.recs) {
+                        const int slot = record_slot(io, ev, score);
+                        if (slot >= 0) {
+                            SeedRecord& R = io.recs[(size_t)ev * REC_SLOTS + slot];
+                            R.round = io.round;
+                            R.index = (int)(my - io.seed_off[ev]);
+                            R.nf = T.nf;
+                            for (int i = 0; i < T.nf; ++i) {
+                                R.key[i] = FL.key[i];
+                                R.r2[i] = FL.r2[i];
+                            }
+                        }
+                    }
                     if (T.flags) atomicOr(&io.flags[ev], T.flags);
                     nsteps += (unsigned long long)T.n;
                     my = -1;
@@ -345,7 +374,7 @@ __global__ void topk_merge_kernel(const int* __restrict__ seg_off, int n_events,
 // rounds, ordered by (E, round, index); seeds decoded from round r's grids.
 __global__ void merge_best_kernel(int n_events, int K, int round, const uint64_t* __restrict__ round_keys,
                                   const cdc_grid* __restrict__ grids, int gpe, uint64_t* best_keys, float* best_E,
-                                  float* best_seed, uint64_t* topk0) {
+                                  float* best_seed, uint64_t* topk0, unsigned* run_best) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_events) return;
     uint64_t ok[CDC_MAX_K];
@@ -380,6 +409,8 @@ __global__ void merge_best_kernel(int n_events, int K, int round, const uint64_t
         for (int a = 0; a < 5; ++a)
             best_seed[((size_t)e * K + i) * 5 + a] = key == KEY_NONE ? __int_as_float(0x7fffffff) : sd[a];
     }
+    // the next round records the seeds that reach this score (record_slot)
+    if (run_best) run_best[e] = bk[0] == KEY_NONE ? 0x7f800000u : (uint32_t)(bk[0] >> 32);
 }
 
 // Zoom grids of round r (sec. 2.2: finer seed sets around the candidates):
@@ -440,10 +471,29 @@ __global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, S
         event_seed(io.grids, io.gpe, ev, (long long)s - io.seed_off[ev], sd);
         T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_rec[threadIdx.x >> 5], sd);
         T.run(G, F, P, s_lay, s_tab);
+        const float score = T.score(P, io.hit_off[ev + 1] - io.hit_off[ev]);
         if (lane == 0) {
-            io.E[s] = T.score(P, io.hit_off[ev + 1] - io.hit_off[ev]);
+            io.E[s] = score;
             if (T.flags) atomicOr(&io.flags[ev], T.flags);
             nsteps += (unsigned long long)T.n;
+        }
+        if (io.recs) {
+            int slot = lane == 0 ? record_slot(io, ev, score) : -1;
+            slot = __shfl_sync(FULL, slot, 0);
+            if (slot >= 0) {
+                SeedRecord& R = io.recs[(size_t)ev * REC_SLOTS + slot];
+                const WarpFound* wr = &s_rec[threadIdx.x >> 5];
+                if (lane == 0) {
+                    R.round = io.round;
+                    R.index = (int)((long long)s - io.seed_off[ev]);
+                    R.nf = T.nf;
+                }
+                for (int i = lane; i < T.nf; i += 32) {
+                    R.key[i] = wr->key[i];
+                    R.r2[i] = wr->r2[i];
+                }
+            }
+            __syncwarp();  // the record is read before the next seed overwrites it
         }
     }
     if (io.steps && lane == 0 && nsteps) atomicAdd(io.steps, nsteps);
@@ -458,7 +508,9 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
                                                      const int32_t* __restrict__ hit_off,
                                                      const int32_t* __restrict__ wire_id,
                                                      const float* __restrict__ best_seed, int K, int8_t* hit_part,
-                                                     float* hit_res2) {
+                                                     float* hit_res2, const uint64_t* __restrict__ best_keys,
+                                                     const SeedRecord* __restrict__ recs,
+                                                     const unsigned* __restrict__ rec_count) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
     __shared__ WarpFound s_rec[4];
@@ -480,6 +532,39 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
             if (hit_res2) hit_res2[h] = P.lam;
         }
         return;
+    }
+    // the best seed came from a zoom round and its record was kept (record_slot):
+    // the same scored wires as tracing it again
+    if (recs) {
+        const uint64_t bk = best_keys[(size_t)e * CDC_MAX_K];
+        const int round = (int)((bk >> ROUND_SHIFT) & 0x1fu), index = (int)(bk & ((1ull << ROUND_SHIFT) - 1));
+        const int n = min(rec_count[e], (unsigned)REC_SLOTS);
+        int slot = -1;
+        for (int b = 0; b < n; b += 32) {
+            const int i = b + lane;
+            const SeedRecord* R = recs + (size_t)e * REC_SLOTS + i;
+            const unsigned m = __ballot_sync(0xffffffffu, i < n && R->round == round && R->index == index);
+            if (m) {
+                slot = b + __ffs(m) - 1;
+                break;
+            }
+        }
+        if (bk != KEY_NONE && round > 0 && slot >= 0) {
+            const SeedRecord& R = recs[(size_t)e * REC_SLOTS + slot];
+            for (int h = h0 + lane; h < h1; h += 32) {
+                const int w = wire_id[h];
+                int part = -1;
+                float r2 = P.lam;
+                for (int i = 0; i < R.nf; ++i)
+                    if ((int)(R.key[i] & 0xffffu) == w) {
+                        part = (int)(R.key[i] >> 16);
+                        r2 = R.r2[i];
+                    }
+                if (hit_part) hit_part[h] = (int8_t)part;
+                if (hit_res2) hit_res2[h] = r2;
+            }
+            return;
+        }
     }
     WarpFound* rec = &s_rec[threadIdx.x >> 5];
     WarpTracer<KIND> T;
@@ -779,6 +864,9 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0);
     const int scan_blocks = num_sms * (occ > 0 ? occ : 1);
+    if (W.rec_count && L.n_rounds > 1 && (L.hit_part || L.hit_res2) &&
+        (err = cudaMemsetAsync(W.rec_count, 0, sizeof(unsigned) * ne, st)) != cudaSuccess)
+        return err;
     for (int r = 0; r < L.n_rounds; ++r) {
         const cdc_grid* grids = r == 0 ? L.grids0 : W.zgrids + (size_t)(r & 1) * W.max_events * CDC_MAX_ZOOM;
         const int gpe = r == 0 ? 1 : CDC_MAX_ZOOM;
@@ -802,8 +890,10 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                                             L.flags);
         if (r == 0 && W.perm)
             order_blocks_kernel<<<ne, 1024, 0, st>>>(ne, grids, G.z_half, P.b_max, P.max_part, P.direction, W.perm);
+        const bool rec = r > 0 && W.recs && (L.hit_part || L.hit_res2);
         ScanIO io{W.drift_tab, L.hit_off, grids, gpe, W.seed_off, ne, W.counters, E, L.flags,
-                  L.steps ? L.steps + r : nullptr, r == 0 ? W.perm : nullptr};
+                  L.steps ? L.steps + r : nullptr, r == 0 ? W.perm : nullptr, rec ? W.recs : nullptr,
+                  W.rec_count, W.run_best, r};
         const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
         if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
         // a round of few seeds (host bound: zoom grids of 3^5 seeds) runs one warp per seed
@@ -833,16 +923,19 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
         uint64_t* rk = W.round_keys + (size_t)(r & 1) * W.max_events * CDC_MAX_K;
         topk_merge_kernel<<<blocks_for((long long)ne * 32, 256), 256, 0, st>>>(W.seg_off, ne, P.k, W.seg_keys, rk);
         merge_best_kernel<<<blocks_for(ne, 64), 64, 0, st>>>(ne, P.k, r, rk, grids, gpe, W.best_keys, L.best_E,
-                                                             L.best_seed, L.topk0);
+                                                             L.best_seed, L.topk0, W.run_best);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (L.hit_part || L.hit_res2) {
+        const SeedRecord* recs = L.n_rounds > 1 ? W.recs : nullptr;
         if (F.kind == 0)
             assign_kernel<0><<<blocks_for(ne, 4), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
-                                                                L.best_seed, P.k, L.hit_part, L.hit_res2);
+                                                                L.best_seed, P.k, L.hit_part, L.hit_res2,
+                                                                W.best_keys, recs, W.rec_count);
         else
             assign_kernel<1><<<blocks_for(ne, 4), 128, 0, st>>>(G, F, P, ne, W.drift_tab, L.hit_off, L.wire_id,
-                                                                L.best_seed, P.k, L.hit_part, L.hit_res2);
+                                                                L.best_seed, P.k, L.hit_part, L.hit_res2,
+                                                                W.best_keys, recs, W.rec_count);
     }
     return cudaGetLastError();
 }

@@ -111,3 +111,30 @@ def test_events_in_flight_equal_events_one_at_a_time(field_map):
     for e, (a, b) in enumerate(zip(alone, outs)):
         for k in keys:
             assert torch.equal(a[k], b[k]), (e, k)
+
+
+def test_classification_from_the_kept_record_equals_tracing_the_best_seed(field_map):
+    """The ten-round scan classifies the hits of its best seed from the record
+    the seed's zoom round kept; scanning a one-seed grid at that seed (one
+    round: the best seed is traced again) gives the same partitions and
+    residuals, bit for bit, and the same score to 1e-6."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    _, _, ev = S.cfg2_case(0, field_map, occupancy=0.10)
+    n0, hp, sp = _config()
+    tr = _tracker(g, field_map, n0)
+    h, out = _scan(tr, ev, hp, sp, n0, want_E=True)
+    torch.cuda.synchronize()
+    assert float(out["best_E"][0, 0]) < float(out["E"].min())   # the best seed comes from a zoom round
+    best = out["best_seed"][0, 0].cpu().numpy()
+    one = np.zeros(1, dtype=cdc.GRID_DTYPE)
+    one["centre"][0] = best
+    one["n"][0] = (1, 1, 1, 1, 1)
+    p1 = cdc.scan_params(h=2.0, max_steps=3500, lam=4.0, max_partitions=3, k=8, n_rounds=1, max_drift=8.0)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    ref = tr.scan(off, wid, dr, cdc.grids_to_tensor(one, tr.dev), p1, want_hits=True)
+    torch.cuda.synchronize()
+    assert abs(float(ref["best_E"][0, 0]) - float(out["best_E"][0, 0])) <= 1e-6 * float(out["best_E"][0, 0])
+    assert torch.equal(ref["hit_part"], out["hit_part"])
+    assert torch.equal(ref["hit_res2"], out["hit_res2"])
