@@ -151,9 +151,12 @@ int cdc_load_field(cdc_ctx* ctx, int kind, float b0, const float* bz, const floa
                    float r_min, float z_min, float dr, float dz);
 
 /* Size the context's workspace for calls with up to max_events events,
- * max_seeds seeds in total per scan round, and max_hits hits.  Compute calls
- * never allocate; a call that exceeds the reservation fails with
- * CDC_ERR_NOT_LOADED.  Errors: CDC_ERR_ARG, CDC_ERR_NOMEM. */
+ * max_seeds seeds in total per scan round, and max_hits hits (besides the
+ * per-seed scores and top-K segments, about 90 KB per event: the hit tables,
+ * the coarse grid's block order and 64 records of scored wires kept for the
+ * classification).  Compute calls never allocate; a call that exceeds the
+ * reservation fails with CDC_ERR_NOT_LOADED.  Errors: CDC_ERR_ARG,
+ * CDC_ERR_NOMEM. */
 int cdc_reserve(cdc_ctx* ctx, int max_events, int64_t max_seeds, int64_t max_hits);
 
 /* ---- compute ------------------------------------------------------------ */
@@ -196,6 +199,8 @@ int cdc_hough_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const in
  * seed), zoom_grids [n_rounds][n_events][n_zoom] (nullable; the grids of each
  * round, round 0 in slot 0), flags [n_events], steps (nullable, [n_rounds]
  * counters: RKN steps executed in each round, added to the current values).
+ * The order in which seeds are processed (coarse grids: blocks of equal
+ * (z0, pz0), longest estimated track first) changes no output.
  * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
 int cdc_scan_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id,
                    const float* drift, const cdc_grid* grids, const cdc_scan_params* params, float* E,
