@@ -75,6 +75,7 @@ def csrc_digest() -> str:
             h.update(fh.read())
     return h.hexdigest()
 H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
+NC_CUT = 20                      # common hits of the entrance and exit scans (sec. 2.2)
 
 
 def flops_per_step(kind: int) -> int:
@@ -348,7 +349,7 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
     # turn 0) per event, averaged over the events that pass N_c >= 20; the
     # other truth turns count as signal partitions in the purity
     truth_t = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=tr.dev)
-    keep = np.flatnonzero(nc >= 20)
+    keep = np.flatnonzero(nc >= NC_CUT)
     quality = {}
     for name, o in zip(("entrance", "exit"), outs):
         C = tr.classification_counts(off_t, o["hit_part"], truth_t, 8).cpu().numpy()
@@ -358,7 +359,7 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
     return {"events": n_ev, "seeds_per_direction": n_seeds, "ms": ms, "events_per_s": n_ev / (ms / 1e3),
             "seeds_per_s": 2 * (n_seeds + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev) / (ms / 1e3),
             "n_common_mean": float(nc.mean()), "n_common_min": int(nc.min()),
-            "pass_nc_ge_20": float(np.mean(nc >= 20)), "turn0_hits_mean": float(turn0.mean()),
+            "pass_nc_ge_20": float(np.mean(nc >= NC_CUT)), "turn0_hits_mean": float(turn0.mean()),
             "classification_nc_ge_20": dict(quality, events=int(keep.size),
                                             definition="Eqs. 2-3 of the scanned turn per event, mean over the "
                                                        "events with N_c >= 20 (the paper: 76 % / 90 % for its "
