@@ -62,7 +62,7 @@ TRAFFIC = {"bytes": 34_452_224 + 16_884_480, "csrc_sha256": "d4353487ae65b2e9d4d
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "csrc_sha256": "d4353487ae65b2e9d4daed806e68bbd731a9dcaa8e3953e2cf6584fe1d9d02de"}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "fma_pipe_active_pct": 36.6, "csrc_sha256": "d4353487ae65b2e9d4daed806e68bbd731a9dcaa8e3953e2cf6584fe1d9d02de"}
 
 
 def csrc_digest() -> str:
@@ -832,6 +832,7 @@ def run_cuda(args, ws, rank, local):
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
                      "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
                      "ncu_fp32": ({"fp32_ops_per_rkn_step": FP32_COUNTS["fp32_ops_per_rkn_step"],
+                                   "fma_pipe_active_pct_240k_case": FP32_COUNTS["fma_pipe_active_pct"],
                                    "executed_tflops": executed,
                                    "executed_fp32_frac_of_peak": executed / peak if executed else None,
                                    "note": "all executed FP32 work (FFMA = 2) per RKN step from ncu, times this "
