@@ -122,12 +122,17 @@ __global__ void prologue_kernel(int n_events, const cdc_grid* __restrict__ grids
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        long long tot = s_base;
-        if (tot > cap || (long long)s_sbase > seg_cap) {  // beyond the buffers: scan nothing, flag every event
-            for (int e = 0; e < n_events; ++e) atomicOr(&flags[e], CDC_FLAG_EMPTY);
-            tot = 0;
+    // beyond the buffers: scan nothing (every event gets empty seed and segment
+    // ranges, so no later kernel reads past them) and flag every event
+    const bool over = s_base > cap || (long long)s_sbase > seg_cap;
+    if (over)
+        for (int e = threadIdx.x; e <= n_events; e += blockDim.x) {
+            seed_off[e] = 0;
+            seg_off[e] = 0;
+            if (e < n_events) atomicOr(&flags[e], CDC_FLAG_EMPTY);
         }
+    if (threadIdx.x == 0) {
+        const long long tot = over ? 0 : s_base;
         seed_off[n_events] = tot;
         seg_off[n_events] = tot ? s_sbase : 0;
         counters[0] = 0;

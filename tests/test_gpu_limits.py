@@ -79,3 +79,36 @@ def test_record_overflow_is_flagged():
         if not overflow:
             bad, _, worst = compare_scores(out["E"].cpu().numpy(), ref)
             assert bad.size == 0, (bad[:10], worst)
+
+
+def test_grids_beyond_the_reserved_capacity_scan_nothing():
+    """Two events whose grids (2 x 4000 seeds) exceed a workspace reserved for
+    3888 scores: without a caller score buffer the call scans nothing and flags
+    both events empty (no best seed, no hit classes); with the caller's buffer
+    for the coarse scores the same call scans normally and equals a tracker
+    with room to spare, bit for bit."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev0, grid0 = S.cfg1_case(6)
+    _, _, ev1, grid1 = S.cfg1_case(7)
+    grids = np.concatenate([grid0, grid1])
+    n = 2 * int(np.prod(grid0["n"][0]))
+    off = np.array([0, ev0.wire_id.size, ev0.wire_id.size + ev1.wire_id.size])
+    wid = np.concatenate([ev0.wire_id, ev1.wire_id])
+    dr = np.concatenate([ev0.drift, ev1.drift])
+    p = cdc.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1, k=8, n_rounds=3, n_zoom=2)
+    small = tracker(g, f, max_events=2, max_seeds=1000)
+    big = tracker(g, f, max_events=2, max_seeds=n)
+    outs = {}
+    for name, tr, want_E in (("over", small, False), ("caller_E", small, True), ("big", big, True)):
+        o, w, d = tr.events_to_device(off, wid, dr)
+        outs[name] = tr.scan(o, w, d, cdc.grids_to_tensor(grids, tr.dev), p, want_E=want_E, n_seeds=n)
+    torch.cuda.synchronize()
+    over = outs["over"]
+    assert np.all(over["flags"].cpu().numpy() & cdc.FLAG_EMPTY)
+    assert np.all(np.isinf(over["best_E"].cpu().numpy()))
+    assert np.all(np.isnan(over["best_seed"].cpu().numpy()))
+    assert np.all(over["hit_part"].cpu().numpy() == -1)
+    assert int(over["steps"].sum()) == 0
+    for key in ("E", "topk0", "best_E", "best_seed", "hit_part", "hit_res2", "flags", "steps"):
+        assert torch.equal(outs["caller_E"][key], outs["big"][key]), key
