@@ -51,8 +51,10 @@ def test_hough_bit_exact_batched(field_map):
 def test_zoom_rounds_follow_oracle_scores():
     """Round r's grids are 3^5 grids with the coarse step times 2^-r centred on a
     valid top-n_zoom of round r-1 (by the oracle's scores, ties within
-    tolerance); the reported best score equals the oracle's score of the
-    reported best seed and is not above the coarse best."""
+    tolerance); each round's best oracle score is not above the previous
+    round's (its grids contain their centres, among them the previous best);
+    the reported best score equals the oracle's score of the reported best seed
+    and is not above the coarse best."""
     import torch
     import paper_1908_01949_gb300 as cdc
     g, f, ev, grid = S.cfg1_case(6)
@@ -82,8 +84,10 @@ def test_zoom_rounds_follow_oracle_scores():
             assert i.size >= 1, (r, c)
             assert prev_E[i[0]] <= kth * (1 + E_REL), (r, c)
             seeds_r.append(O.grid_values(gr))
+        prev_best = prev_E.min()
         prev_seeds = np.concatenate(seeds_r)
         prev_E = O.scan(g, f, ev.wire_id, drift, prev_seeds, op)["E"]
+        assert prev_E.min() <= prev_best, (r, prev_E.min(), prev_best)
     best = out["best_seed"][0, 0].cpu().numpy().astype(np.float64)
     ref = O.scan(g, f, ev.wire_id, drift, best[None], op)["E"][0]
     bE = out["best_E"][0].cpu().numpy()
