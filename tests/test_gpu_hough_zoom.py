@@ -87,7 +87,7 @@ def test_zoom_rounds_follow_oracle_scores():
         prev_best = prev_E.min()
         prev_seeds = np.concatenate(seeds_r)
         prev_E = O.scan(g, f, ev.wire_id, drift, prev_seeds, op)["E"]
-        assert prev_E.min() <= prev_best, (r, prev_E.min(), prev_best)
+        assert prev_E.min() <= prev_best * (1 + E_REL), (r, prev_E.min(), prev_best)
     best = out["best_seed"][0, 0].cpu().numpy().astype(np.float64)
     ref = O.scan(g, f, ev.wire_id, drift, best[None], op)["E"][0]
     bE = out["best_E"][0].cpu().numpy()
