@@ -505,8 +505,10 @@ __global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, S
 }
 
 // Hit classification of each event's best seed (sec. 2.2: hits with
-// d^2 < lambda belong to the partition under investigation): one warp per
-// event follows the seed (warp_tracer.cuh), then the lanes classify the hits.
+// d^2 < lambda belong to the partition under investigation), one warp per
+// event: from the record of scored wires the seed's zoom round kept
+// (record_slot), else by following the seed again (warp_tracer.cuh); then the
+// lanes classify the hits.
 template <int KIND>
 __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, ScanConst P, int n_events,
                                                      const float* __restrict__ drift_tab,
