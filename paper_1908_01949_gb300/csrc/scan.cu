@@ -217,8 +217,11 @@ __global__ void __launch_bounds__(1024) order_blocks_kernel(int n_events, const 
 // scan order (neighbours in theta0, px0, py0 at equal z0, pz0: nearly the same
 // path, so the lanes search nearly the same wires and stay converged) from a
 // global counter, steps them in chunks of CHUNK RKN steps, and takes the next
-// 32 once all its lanes have ended.  Scores are written at the seeds' row-major
-// indices.
+// 32 once all its lanes have ended; in a coarse round the (z0, pz0) blocks
+// come longest estimated track first (order_blocks_kernel), so the round ends
+// on short tracks.  Scores are written at the seeds' row-major indices; in
+// zoom rounds a seed that reaches its event's best score so far also keeps
+// its record of scored wires (record_slot).
 // BS threads per block, 768 resident threads per SM for every shape (the
 // register budget stays 80 per thread).
 template <int KIND, int BS, int CHUNK>
