@@ -54,7 +54,7 @@ typedef enum {
 /* Per-event warning flags (bitmask). */
 #define CDC_FLAG_STEP_CAP 1u        /* some seed stopped at max_steps */
 #define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed found more than CDC_MAX_FOUND wires below lambda */
-#define CDC_FLAG_EMPTY 4u           /* no hits, no seeds, or no Hough candidate */
+#define CDC_FLAG_EMPTY 4u           /* no hits, no seeds, no Hough candidate, or grids beyond the reservation */
 #define CDC_FLAG_NOT_SPD 8u         /* refine: normal matrix regularised */
 #define CDC_FLAG_DOCA_ZERO 16u      /* refine: a hit at zero distance was left out */
 #define CDC_FLAG_LOST_HIT 32u       /* refine: an assigned hit had no minimum in its partition */
