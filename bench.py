@@ -57,30 +57,44 @@ FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
 SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune_scan's timings
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
 # single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
-# kernel sources it was taken on (csrc_digest: SHA-256 over the csrc files without comments), else null.
-TRAFFIC = {"bytes": 34_728_448 + 16_658_176, "csrc_sha256": "fa1a5a449ea84c00e0cb78ef124f763e1a68ed6e1c07b3acd5c06fb2da0aff21"}
+# kernel sources it was taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
+TRAFFIC = {"bytes": 34_728_448 + 16_658_176, "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "fma_pipe_active_pct": 36.6, "csrc_sha256": "fa1a5a449ea84c00e0cb78ef124f763e1a68ed6e1c07b3acd5c06fb2da0aff21"}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "fma_pipe_active_pct": 36.6, "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
 
 
 def csrc_digest() -> str:
-    """SHA-256 over the kernel sources with comments and whitespace removed:
-    what the compiled kernels depend on, so that a comment edit keeps a
-    measurement valid and a code edit voids it."""
+    """SHA-256 over the sources the recorded scan-kernel counters depend on:
+    the translation units that define and launch the scan kernel (scan.cu,
+    capi.cu) and every header they include, with comments and whitespace
+    removed, so that a comment edit, or a code edit in another translation
+    unit (refine.cu, hough.cu, ...), keeps a measurement valid and an edit of
+    the scan kernel's own code voids it."""
     import hashlib
     import re
     d = os.path.join(ROOT, "paper_1908_01949_gb300", "csrc")
+    files, todo = set(), [os.path.join(d, "scan.cu"), os.path.join(d, "capi.cu")]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in files:
+            continue
+        files.add(f)
+        with open(f, encoding="utf-8") as fh:
+            for inc in re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M):
+                todo.append(os.path.join(os.path.dirname(f), inc))
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        h.update(f.encode())
-        with open(os.path.join(d, f), encoding="utf-8") as fh:
+    for f in sorted(files, key=lambda f: os.path.relpath(f, ROOT)):
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, encoding="utf-8") as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()
+
+
 H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
 NC_CUT = 20                      # common hits of the entrance and exit scans (sec. 2.2)
 

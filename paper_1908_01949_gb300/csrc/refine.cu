@@ -92,7 +92,8 @@ __device__ __forceinline__ void field_grad(const DevField& F, const float r[3], 
     u -= (float)i;
     v -= (float)j;
     const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
-    const float4 qz = __ldg(c), qr = __ldg(c + 1);
+    float4 qz, qr;
+    load_cell(c, qz, qr);
     const float bz = fmaf(v, fmaf(qz.w, u, qz.z), fmaf(qz.y, u, qz.x));
     const float br = fmaf(v, fmaf(qr.w, u, qr.z), fmaf(qr.y, u, qr.x));
     const float cx = r[0] * rinv, cy = r[1] * rinv;
@@ -175,6 +176,52 @@ struct Stages {
         for (int a = 0; a < 3; ++a) k4[a] = lam * c[a];
     }
 };
+
+// One step of rkn_step<KIND, true> that keeps its stage values for the
+// tangent step: the field and its gradient are evaluated once at each stage
+// point, for the state and the tangents together.  The slopes k carry the
+// two-float lam, as in the state step.
+template <int KIND>
+__device__ __forceinline__ void rkn_step_stages(const DevField& F, State& s, float h, float h6_lo, Stages<KIND>& S) {
+    const float h2 = 0.5f * h, hh8 = h * h * 0.125f, hh2 = h * h * 0.5f, hh6 = h * h * (1.0f / 6.0f),
+                h6 = h * (1.0f / 6.0f);
+    const float r[3] = {s.rx, s.ry, s.rz};
+    float rm[3], re[3];
+    S.t1[0] = s.tx;
+    S.t1[1] = s.ty;
+    S.t1[2] = s.tz;
+    field_grad<KIND>(F, r, S.B1, S.g1);
+    kvec<true>(s, S.t1[0], S.t1[1], S.t1[2], S.B1[0], S.B1[1], S.B1[2], S.k1[0], S.k1[1], S.k1[2]);
+    for (int a = 0; a < 3; ++a) {
+        S.t2[a] = fmaf(h2, S.k1[a], S.t1[a]);
+        rm[a] = fmaf(hh8, S.k1[a], fmaf(h2, S.t1[a], r[a]));
+    }
+    field_grad<KIND>(F, rm, S.B2, S.g2);
+    kvec<true>(s, S.t2[0], S.t2[1], S.t2[2], S.B2[0], S.B2[1], S.B2[2], S.k2[0], S.k2[1], S.k2[2]);
+    for (int a = 0; a < 3; ++a) S.t3[a] = fmaf(h2, S.k2[a], S.t1[a]);
+    kvec<true>(s, S.t3[0], S.t3[1], S.t3[2], S.B2[0], S.B2[1], S.B2[2], S.k3[0], S.k3[1], S.k3[2]);
+    for (int a = 0; a < 3; ++a) {
+        S.t4[a] = fmaf(h, S.k3[a], S.t1[a]);
+        re[a] = fmaf(hh2, S.k3[a], fmaf(h, S.t1[a], r[a]));
+    }
+    field_grad<KIND>(F, re, S.B4, S.g4);
+    kvec<true>(s, S.t4[0], S.t4[1], S.t4[2], S.B4[0], S.B4[1], S.B4[2], S.k4[0], S.k4[1], S.k4[2]);
+    // the state update of rkn_step<KIND, true>
+    float d[3], dl[3], tl[3];
+    const float cl[3] = {h * s.mx, h * s.my, h * s.mz};  // h t_lo, straight into the low word
+    for (int a = 0; a < 3; ++a) {
+        d[a] = fmaf(h, S.t1[a], hh6 * (S.k1[a] + S.k2[a] + S.k3[a]));
+        const float sa = S.k1[a] + S.k4[a] + 2.0f * (S.k2[a] + S.k3[a]);
+        tl[a] = h6 * sa;
+        dl[a] = fmaf(h6_lo, sa, fmaf(h6, sa, -tl[a]));
+    }
+    acc2(s.rx, s.lx, d[0], cl[0]);
+    acc2(s.ry, s.ly, d[1], cl[1]);
+    acc2(s.rz, s.lz, d[2], cl[2]);
+    acc2(s.tx, s.mx, tl[0], dl[0]);
+    acc2(s.ty, s.my, tl[1], dl[1]);
+    acc2(s.tz, s.mz, tl[2], dl[2]);
+}
 
 // Tangent of one step: (dr, dt) of five directions, dlam constant.
 template <int KIND>
@@ -521,11 +568,11 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
                     odt[m][a] = dt[m][a];
                 }
             Stages<KIND> S;
-            const float r[3] = {s.rx, s.ry, s.rz}, t[3] = {s.tx, s.ty, s.tz};
-            S.eval(F, r, t, s.lam, h);
+            rkn_step_stages<KIND>(F, s, h, P.h6_lo, S);
             tangent_step<KIND>(S, s.lam, h, dr, dt, dl);
+        } else {
+            rkn_step<KIND, true>(F, s, h, P.h6_lo);
         }
-        rkn_step<KIND, true>(F, s, h, P.h6_lo);
         ++n;
         const float nn[6] = {s.rx, s.ry, s.rz, s.tx, s.ty, s.tz}, nl[3] = {s.lx, s.ly, s.lz};
         const int pt = part;
