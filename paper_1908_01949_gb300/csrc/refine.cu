@@ -710,6 +710,23 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
             rb[1] += A.D[q] * A.ny[q];
             rb[2] += A.D[q] * A.nz[q];
         }
+    // entries with a minimum inside a segment, by segment descending (the
+    // sweep's order) and by entry within a segment (insertion sort, stable):
+    // the sweep takes them with a moving pointer instead of a scan of A per step
+    uint8_t ord[CDC_MAX_FOUND];
+    int n_ord = 0;
+    for (int q = 0; q < A.n; ++q)
+        if (A.j[q] >= 0) {
+            const int jq = A.j[q];
+            int b = n_ord - 1;
+            while (b >= 0 && A.j[ord[b]] < jq) {
+                ord[b + 1] = ord[b];
+                --b;
+            }
+            ord[b + 1] = (uint8_t)q;
+            ++n_ord;
+        }
+    int next = 0;
     const int nblocks = (n + ck_every - 1) / ck_every;
     for (int b = nblocks - 1; b >= 0; --b) {
         const int j0 = b * ck_every, j1 = min(n, j0 + ck_every);  // steps j0 .. j1-1 (state j -> j+1)
@@ -727,8 +744,8 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
         for (int j = j1 - 1; j >= j0; --j) {
             // minima inside segment j: P = a0 r_j + a1 t_j + b0 r_j+1 + b1 t_j+1
             float pr[3] = {0.f, 0.f, 0.f}, ptt[3] = {0.f, 0.f, 0.f};
-            for (int q = 0; q < A.n; ++q) {
-                if (A.j[q] != j) continue;
+            for (; next < n_ord && A.j[ord[next]] == j; ++next) {
+                const int q = ord[next];
                 float a0, a1, b0, b1;
                 hermite_w(A.u[q], h, a0, a1, b0, b1);
                 const float nv[3] = {A.D[q] * A.nx[q], A.D[q] * A.ny[q], A.D[q] * A.nz[q]};
