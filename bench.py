@@ -58,7 +58,7 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
 # single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
 # kernel sources it was taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
-TRAFFIC = {"bytes": 34_728_448 + 16_658_176, "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
+TRAFFIC = {"bytes": 34_728_448 + 16_658_176, "shape": "256x16", "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
@@ -851,7 +851,10 @@ def run_cuda(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
-                     "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/)",
+                     "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/) at launch shape "
+                                     f"{TRAFFIC['shape']} (block x chunk); this run's shape "
+                                     f"{tuned[0]}x{tuned[1]}: the shapes run the same per-seed code and "
+                                     "differ in threads per block and steps between seed refills",
                      "ncu_fp32": ({"fp32_ops_per_rkn_step": FP32_COUNTS["fp32_ops_per_rkn_step"],
                                    "fma_pipe_active_pct_240k_case": FP32_COUNTS["fma_pipe_active_pct"],
                                    "executed_tflops": executed,
