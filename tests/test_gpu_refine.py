@@ -132,3 +132,32 @@ def test_autograd_function_backward_is_the_adjoint_gradient():
     assert torch.equal(c.detach(), ref["chi2"])
     expect = (w.float()[:, None] * ref["grad"]).cpu().numpy()
     assert np.allclose(x.grad.cpu().numpy(), expect, rtol=1e-6, atol=0)
+
+
+def test_empty_call_and_a_seed_whose_event_has_no_hits():
+    """n_seeds = 0 is a no-op.  A seed of an event without hits classifies no
+    hit: chi^2 = 0, no hit used, zero gradient, the normal matrix flagged and
+    the seed left where it was.  A seed's outputs do not depend on the other
+    seeds of the launch: refined beside the empty event's seed, the seed of the
+    event with hits gives the bits it gives alone."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g, f, ev, seeds, mp, ms = _cases("uniform")
+    tr = tracker(g, f)
+    n = ev.wire_id.size
+    off, wid, dr = tr.events_to_device([0, n, n], ev.wire_id, ev.drift)     # event 1 has no hits
+    sp = cdc.scan_params(h=2.0, max_steps=ms, lam=4.0, max_partitions=mp)
+    rp = cdc.refine_params(n_iter=3, sigma=0.2, checkpoint=128)
+    x = torch.as_tensor(seeds[:2], device=tr.dev)
+    none = tr.refine(torch.zeros(0, dtype=torch.int32, device=tr.dev), x[:0], off, wid, dr, sp, rp)
+    assert none["seeds"].shape == (0, 5) and none["chi2"].shape == (0,)
+    both = tr.refine(torch.tensor([1, 0], dtype=torch.int32, device=tr.dev), x, off, wid, dr, sp, rp)
+    alone = tr.refine(torch.tensor([0], dtype=torch.int32, device=tr.dev), x[1:].contiguous(), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    assert float(both["chi2"][0]) == 0.0 and int(both["n_used"][0]) == 0
+    assert torch.all(both["grad"][0] == 0)
+    assert torch.equal(both["seeds"][0], x[0])
+    assert int(both["flags"][0]) & cdc.FLAG_NOT_SPD
+    assert int(both["n_used"][1]) > 0 and float(both["chi2"][1]) > 0.0
+    for k in ("seeds", "chi2", "grad", "n_used", "flags"):
+        assert torch.equal(both[k][1:], alone[k]), k
