@@ -695,7 +695,6 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
         }
         const double r = ((double)A.D[q] - (double)A.drift[q]) / sigma;
         chi2 += r * r;
-        A.u[q] = A.u[q];  // keep
         A.D[q] = (float)(2.0 * r / sigma);  // reuse D as the injection coefficient
         ++used;
     }
