@@ -307,10 +307,10 @@ int cdc_tune_scan(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int3
  * 1..6900), CDC_ERR_NOMEM. */
 int cdc_reserve_split(cdc_ctx* ctx, int chunk, int max_steps);
 
-/* The coarse scan organised as in the paper's "kernel function separation"
- * (sec. 4.2): for `chunk` seeds at a time, kernel A (one thread per seed) records
- * the state after every RKN step to the end of the track, then kernel B (one
- * block per seed, threads over the event's hits: the block-per-seed,
+/* The coarse scan organised as the paper's two separate kernels (sec. 4.2:
+ * propagation, then the distance search): for `chunk` seeds at a time, kernel
+ * A (one thread per seed) records the state after every RKN step to the end of
+ * the track, then kernel B (one block per seed, threads over the event's hits: the block-per-seed,
  * thread-per-wire layout of sec. 2.2) finds every hit's distance of closest
  * approach from the recorded states and sums Eq. 1.  Same minima and scores as
  * cdc_scan_seeds (up to the order of the Eq. 1 sum), one round only, scores

@@ -1,5 +1,6 @@
-// The paper's two-kernel organisation of the scan (arXiv:1908.01949 sec. 4.2,
-// "kernel function separation"), kept as an A/B reference for the fused scan:
+// The paper's two-kernel organisation of the scan (arXiv:1908.01949 sec. 4.2:
+// propagation and distance search in separate kernels), kept as an A/B
+// reference for the fused scan:
 //   A. one thread per seed propagates the seed to the end of its track and
 //      records the state after every RKN step;
 //   B. one block per seed and one thread per hit of the event (the paper's
