@@ -819,6 +819,8 @@ def run_cuda(args, ws, rank, local):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
+        if refine is not None:
+            cpu["refine"] = guarded('cpu_refine', lambda: cpu_refine_baseline(g, fm, args.refine_events))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -917,6 +919,32 @@ def cpu_baseline(ev, g, fm, grid_t, target_s=15.0):
                          "sample": f"{done1} seeds, {t1:.1f} s, one thread"},
             "sample": f"{done} seeds drawn at random from the step's 10^6-seed coarse grid, same event and "
                       f"parameters, {t:.1f} s"}
+
+
+def cpu_refine_baseline(g, fm, n_dist, target_s=3.0):
+    """FP64 oracle refinement, one thread, on a bounded sample: seeds near
+    the first-turn truth of the refine leg's distinct events (seeded noise),
+    each classified at its start and refined with the leg's iterations."""
+    import cdc_synth as S
+    import oracle as O
+    P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
+    evs = [S.cfg2_case(10_000 + i, fm, occupancy=0.10)[2] for i in range(max(1, n_dist))]
+    rng = np.random.default_rng(4)
+    sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * 0.3
+    t, done = 0.0, 0
+    while t < target_s:
+        ev = evs[done % len(evs)]
+        sd = ev.truth_seeds[0] + rng.normal(0.0, 1.0, 5) * sig
+        drift = ev.drift.astype(np.float64)
+        t0 = time.perf_counter()
+        part = O.scan(g, fm, ev.wire_id, drift, sd[None], P, per_hit=True, threads=1)["hit_part"][0]
+        O.refine(g, fm, P, ev.wire_id, drift, part, sd, n_iter=REFINE_ITER, sigma=REFINE_SIGMA)
+        t += time.perf_counter() - t0
+        done += 1
+    return {"value": done / t, "unit": "seeds/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} seeds near the first-turn truth of {len(evs)} of the refine leg's events, "
+                      f"classification and {REFINE_ITER} Gauss-Newton iterations with the FP64 tangent gradient, "
+                      f"{t:.1f} s, one thread"}
 
 
 # --------------------------------------------------------- reference arm
