@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the seed-scanning track finder (arXiv:1908.01949).
 
-TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
-leg of the benchmark are the only users.  The arithmetic lives in oracle.c
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg and reference arm are the only users.  The arithmetic lives in oracle.c
 (plain C, double precision); this module builds it with gcc, marshals numpy
 arrays through ctypes, and adds the steps that are library primitives (sort
 for the top-K) or plain control flow (the ten-round zoom of sec. 2.2).

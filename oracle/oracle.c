@@ -2,8 +2,8 @@
  * FP64 CPU oracle for the seed-scanning track finder of
  * "GPU Tracking in the COMET Phase-I Cylindrical Drift Chamber" (arXiv:1908.01949).
  *
- * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
- * baseline leg of the benchmark may load this file's library.  It shares no
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg and reference arm may load this file's library.  It shares no
  * code, header or table with the CUDA library: it rebuilds the wire table, the
  * Hough offsets and every formula from the definitions below, plainly, in
  * double precision, with no blocking or reordering beyond what the definitions
