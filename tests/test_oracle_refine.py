@@ -108,3 +108,19 @@ def test_gauss_newton_recovers_noiseless_truth():
     assert np.all(np.abs((so - truth) / SCALE) < 1e-7)
     c0 = O.chi2(g, f, P, ev.wire_id, drift, part, start)[0]
     assert c0 > 50.0
+
+
+def test_no_classified_hit_leaves_the_seed_and_flags_the_system():
+    """An event without hits: chi^2 is an empty sum (0), its gradient is zero,
+    the 5x5 normal matrix is zero (not positive definite, flagged) and the
+    seed stays where it was."""
+    g, f, ev, _ = S.cfg1_case(7)
+    P = O.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1)
+    sd = ev.truth_seeds[0].astype(np.float64)
+    none_i, none_f = np.zeros(0, np.int32), np.zeros(0)
+    so, c2, gr, nu, fl = O.refine(g, f, P, none_i, none_f, none_i, sd, n_iter=3)
+    assert c2 == 0.0 and nu == 0 and np.all(gr == 0.0)
+    assert np.array_equal(so, sd)
+    assert fl & 8
+    c2b, grb = O.chi2(g, f, P, none_i, none_f, none_i, sd)[:2]
+    assert c2b == 0.0 and np.all(grb == 0.0)
