@@ -168,6 +168,46 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+THROTTLE_REJECT = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clock_rejection(clocks):
+    """Why a timed region's clock record rejects its number, else None: a
+    hardware or thermal slowdown seen during it, or SM clocks held well below
+    their maximum with no reason reported (a leftover clock lock).  A power cap
+    (sw_power_cap) is kept and stays noted in the record."""
+    bad = [r for r in clocks.get("reasons", []) if r in THROTTLE_REJECT]
+    if bad:
+        return "throttled: " + ", ".join(bad)
+    sm, smax = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    if sm and smax and sm < 0.85 * smax and not clocks.get("reasons"):
+        return f"SM clock {sm:.0f} of {smax:.0f} MHz with no reason reported"
+    return None
+
+
+def timed_region(run, sampler, sync, dist=None, device=None):
+    """run() between barriers and device synchronisations under the clock
+    sampler.  If any rank's clock record rejects the run, every rank runs it
+    once more and the second run is kept, with the reason the first was
+    rejected in the clock record."""
+    def once():
+        if dist:
+            dist.barrier()
+        sync()
+        sampler.start()
+        out = run()
+        if dist:
+            dist.barrier()
+        return out, sampler.stop()
+
+    out, clocks = once()
+    why = clock_rejection(clocks)
+    if reduce_max(1.0 if why else 0.0, dist, device) > 0.0:
+        out, clocks = once()
+        clocks["first_run_rejected"] = why or "clock record of another rank"
+    return out, clocks
+
+
 def grid_for_tuning(ctx, ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream):
     """The step's seed grid (Hough output), computed once before tuning."""
     ctx.cdc_hough_seeds(ne, off, wid, hp, acc, cand, ncand, grid, hflags, stream)
@@ -770,14 +810,7 @@ def run_cuda(args, ws, rank, local):
 
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    dev_ms, wall = run_stream()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
+    (dev_ms, wall), clocks = timed_region(run_stream, sampler, torch.cuda.synchronize, dist, dev)
     ms = reduce_max(dev_ms / args.steps, dist, dev)
     rkn_per_step = float(sum(q["steps"].sum().item() for q in slots)) / args.steps
     # roofline of the dominant kernel (coarse-round scan launch), ALU bound
