@@ -37,7 +37,7 @@ extern "C" {
 #define CDC_MAX_K 64
 #define CDC_MAX_ZOOM 8
 #define CDC_MAX_ROUNDS 16
-#define CDC_MAX_FOUND 128 /* per-seed list of wires scored below lambda */
+#define CDC_MAX_FOUND 128 /* per-seed record: wires passed closer than drift + sqrt(lambda) */
 
 typedef struct cdc_ctx cdc_ctx;
 
@@ -53,7 +53,7 @@ typedef enum {
 
 /* Per-event warning flags (bitmask). */
 #define CDC_FLAG_STEP_CAP 1u        /* some seed stopped at max_steps */
-#define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed found more than CDC_MAX_FOUND wires below lambda */
+#define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed passed more than CDC_MAX_FOUND fired wires within drift + sqrt(lambda) */
 #define CDC_FLAG_EMPTY 4u           /* no hits, no seeds, no Hough candidate, or grids beyond the reservation */
 #define CDC_FLAG_NOT_SPD 8u         /* refine: normal matrix regularised */
 #define CDC_FLAG_DOCA_ZERO 16u      /* refine: a hit at zero distance was left out */
@@ -254,10 +254,22 @@ int cdc_propagate(cdc_ctx* ctx, int n_seeds, const float* seeds, const cdc_scan_
  * 1024 launches.  cdc_kernel_time waits for the recorded events, returns the
  * summed device time [ms], the number of timed launches since the last read
  * and (per_launch_ms nullable, host, cap entries) each launch's time in launch
- * order, and clears them.  Do not enable it while capturing a CUDA graph.
- * Errors: CDC_ERR_ARG, CDC_ERR_CUDA. */
+ * order, and clears them.  enable: 0 off; 1 on; 2 on for a scan captured into
+ * a CUDA graph: the marks become event-record nodes of the graph, every
+ * replay records them again, and reads do not clear them (read after each
+ * replay; enabling again clears them).  Errors: CDC_ERR_ARG, CDC_ERR_CUDA. */
 int cdc_kernel_timer(cdc_ctx* ctx, int enable);
 int cdc_kernel_time(cdc_ctx* ctx, double* total_ms, int64_t* launches, float* per_launch_ms, int cap);
+
+/* FP32 FMA throughput of the context's GPU (measurement aid, no counterpart
+ * in the paper): the denominator of the scan kernel's FP32 roofline.  Launches
+ * a kernel in which every thread runs eight independent FMA chains of
+ * 16 * iters FMAs each, on every SM at full occupancy, once to warm up and
+ * once timed with CUDA events on `stream`; synchronous.  Outputs (host):
+ * tflops = 2 FMAs / time [TFLOP/s], ms = the timed launch.  iters 1 .. 2^20
+ * (4096 runs ~4 ms on a GB300).  Errors: CDC_ERR_ARG, CDC_ERR_RANGE,
+ * CDC_ERR_CUDA. */
+int cdc_fp32_peak(cdc_ctx* ctx, int iters, double* tflops, double* ms, void* stream);
 
 /* ---- launch shape of the seed scan and its autotuner -------------------- */
 
@@ -386,10 +398,16 @@ int cdc_common_hits(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const in
  * calls no cudaMalloc, cudaFree or allocating library routine.
  * Limits: n_events <= CDC_NOALLOC_MAX_EVENTS and n_seeds (the number of seeds
  * the grids hold, stated by the caller) <= CDC_NOALLOC_MAX_SEEDS, else
- * CDC_ERR_RANGE; if the grids hold more seeds than that on the device, every
- * event is flagged CDC_FLAG_EMPTY and nothing is scanned.
+ * CDC_ERR_RANGE; if the grids hold more than n_seeds seeds on the device
+ * (whether E is given or not), every event is flagged CDC_FLAG_EMPTY and
+ * nothing is scanned or written to E.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress), which can load the library's device code and back
+ * the array with device memory at that moment (lazy module loading): make
+ * that first call at start-up, before any stream capture and outside any
+ * context that forbids allocation.  The address is kept for the life of the
+ * process; resetting the device's primary context (cudaDeviceReset) is not
+ * supported, as for every other call of the context.
  * All calls share the one array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and corrupt each other's results, so
  * serialise them.  Errors as cdc_scan_seeds. */

@@ -36,7 +36,7 @@ EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
            "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_extrapolate_turn", "cdc_classification_counts",
-           "cdc_common_hits",
+           "cdc_common_hits", "cdc_fp32_peak",
            "cdc_scan_seeds_noalloc"]
 
 
@@ -377,7 +377,14 @@ class Context:
         return (best.block, best.chunk), [float(x) for x in ms]
 
     def cdc_kernel_timer(self, enable):
-        return self._check(self.L.cdc_kernel_timer(self.h, int(bool(enable))))
+        """enable: False/0 off, True/1 on, 2 on for a scan captured into a CUDA graph."""
+        return self._check(self.L.cdc_kernel_timer(self.h, int(enable)))
+
+    def cdc_fp32_peak(self, iters=4096, stream=None):
+        """(TFLOP/s, ms) of the FP32 FMA throughput kernel (synchronous)."""
+        tf, ms = C.c_double(0), C.c_double(0)
+        self._check(self.L.cdc_fp32_peak(self.h, int(iters), C.byref(tf), C.byref(ms), _stream(stream)))
+        return tf.value, ms.value
 
     def cdc_kernel_time(self, cap=2048):
         """(summed device ms, launches, per-launch ms) of the timed scan-kernel launches."""

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcdc.so")
-SOURCES = ["capi.cu", "scan.cu", "hough.cu", "refine.cu", "noalloc.cu", "split.cu"]
+SOURCES = ["capi.cu", "scan.cu", "hough.cu", "refine.cu", "noalloc.cu", "split.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

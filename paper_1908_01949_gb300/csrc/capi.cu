@@ -48,9 +48,12 @@ struct cdc_ctx {
     // scan-kernel launch shape (cdc_scan_config)
     int scan_block = 256, scan_chunk = 16, scan_warp_seeds = 0;
     // kernel timer
-    bool timer_on = false;
+    bool timer_on = false, timer_keep = false;
     std::vector<cudaEvent_t> timer_ev;
     int timer_used = 0;
+    // FP32 throughput measurement
+    float* d_sink = nullptr;
+    int sink_n = 0;
 };
 
 namespace {
@@ -191,6 +194,7 @@ void cdc_destroy(cdc_ctx* c) {
     dfree(c->split_n);
     dfree(c->split_end);
     for (cudaEvent_t e : c->timer_ev) cudaEventDestroy(e);
+    dfree(c->d_sink);
     delete c;
 }
 
@@ -729,6 +733,7 @@ int cdc_kernel_timer(cdc_ctx* c, int enable) {
             if (cudaEventCreate(&e) != cudaSuccess) return fail(c, CDC_ERR_CUDA, "cudaEventCreate");
     }
     c->timer_on = enable != 0;
+    c->timer_keep = enable == 2;
     c->timer_used = 0;
     return CDC_OK;
 }
@@ -748,7 +753,42 @@ int cdc_kernel_time(cdc_ctx* c, double* total_ms, int64_t* launches, float* per_
     }
     *total_ms = tot;
     *launches = c->timer_used / 2;
-    c->timer_used = 0;
+    if (!c->timer_keep) c->timer_used = 0;
+    return CDC_OK;
+}
+
+int cdc_fp32_peak(cdc_ctx* c, int iters, double* tflops, double* ms, void* stream) {
+    if (!c || !tflops || !ms) return c ? fail(c, CDC_ERR_ARG, "NULL argument") : CDC_ERR_ARG;
+    if (iters < 1 || iters > (1 << 20)) return fail(c, CDC_ERR_RANGE, "iters outside 1..2^20");
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int need = c->num_sms * 64;  // >= blocks of one launch (at most 8 blocks of 256 threads per SM)
+    cudaError_t e;
+    if (c->sink_n < need) {
+        dfree(c->d_sink);
+        c->sink_n = 0;
+        if ((e = dalloc(c->d_sink, (size_t)need)) != cudaSuccess) return cuda_fail(c, e, "sink allocation");
+        c->sink_n = need;
+    }
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return fail(c, CDC_ERR_CUDA, "cudaEventCreate");
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(c, CDC_ERR_CUDA, "cudaEventCreate");
+    }
+    double fmas = 0.0;
+    float t = 0.f;
+    e = launch_ffma(c->num_sms, iters, c->d_sink, st, &fmas);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_ffma(c->num_sms, iters, c->d_sink, st, &fmas);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "FP32 peak measurement");
+    *ms = t;
+    *tflops = 2.0 * fmas / (t * 1e-3) / 1e12;
     return CDC_OK;
 }
 

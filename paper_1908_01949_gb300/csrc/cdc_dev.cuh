@@ -290,13 +290,15 @@ __device__ __forceinline__ void grid_seed(const cdc_grid& g, long long idx, floa
 constexpr int PERM_CAP = 4096;  // (z0, pz0) blocks of a coarse grid that can be reordered
 constexpr int REC_SLOTS = 64;   // per event: records of zoom-round seeds that reached the event's best score
 
-// The scored wires of one zoom-round seed (wire | partition << 16 and res^2,
-// its hit classification), kept when the seed's score was at most the best of
-// its event so far: the final best seed of a zoom round is then among them.
+// The record of one zoom-round seed (the entries of the tracer's FoundList,
+// from which its hits are classified), kept when the seed's score was at most
+// the best of its event so far: the final best seed of a zoom round is then
+// among them.
 struct SeedRecord {
     int round, index, nf, pad;
     uint32_t key[CDC_MAX_FOUND];
-    float r2[CDC_MAX_FOUND];
+    float r[CDC_MAX_FOUND];
+    float cd[CDC_MAX_FOUND];
 };
 
 // Row-major index of the q-th seed of a grid in scan order: (z0, pz0)

@@ -53,6 +53,7 @@ struct ScanLaunch {
     KernelTimer timer;
     int block = 256, chunk = 16;  // scan-kernel launch shape (cdc_scan_config)
     long long warp_seeds = 0;     // zoom rounds of at most this many seeds run one warp per seed
+    long long e0_cap = -1;        // >= 0: most seeds the coarse round may hold (E0 and workspace sized for it)
 };
 
 // Kernel launchers (scan.cu).  Return cudaSuccess or the launch error.
@@ -139,5 +140,9 @@ struct RefineLaunch {
 };
 cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& P, const RefineLaunch& L,
                           float* drift_tab, int num_sms, int do_gn, cudaStream_t st);
+
+// FP32 FMA throughput measurement (peak.cu): one launch filling every SM;
+// fma_count = FMAs it executes.  sink: device float[grid] (written never).
+cudaError_t launch_ffma(int num_sms, int iters, float* sink, cudaStream_t st, double* fma_count);
 
 }  // namespace cdc

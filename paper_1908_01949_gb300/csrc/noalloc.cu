@@ -133,6 +133,9 @@ extern "C" int cdc_scan_seeds_noalloc(cdc_ctx* c, int n_events, int64_t n_seeds,
                  flags, steps, 1, 1, KernelTimer{}};
     L.block = block;
     L.chunk = chunk;
+    // the caller sized E (and the array holds the scores) for n_seeds: grids that
+    // hold more scan nothing and flag every event empty, with or without E
+    L.e0_cap = n_seeds;
     e = launch_scan(G, F, P, W, L, sms, st);
     if (e != cudaSuccess) return set_error(c, CDC_ERR_CUDA, cudaGetErrorString(e));
     return CDC_OK;

@@ -829,8 +829,12 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
         while (T.step(G, F, P, s_lay, s_tab, FL))
             if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
         flags |= T.flags;
-        A.n = T.nf;
-        for (int q = 0; q < T.nf; ++q) A.key[q] = FL.key[q];
+        A.n = 0;
+        for (int q = 0; q < T.nf; ++q) {
+            int part;
+            entry_class(FL.key[q], FL.r[q], FL.cd[q], P.lam, part);
+            if (part >= 0) A.key[A.n++] = (uint32_t)key_wire(FL.key[q]) | ((uint32_t)part << 16);
+        }
     }
     for (int q = 1; q < A.n; ++q) {  // sort by wire
         const uint32_t k = A.key[q];

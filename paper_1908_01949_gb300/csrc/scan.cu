@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                             R.nf = T.nf;
                             for (int i = 0; i < T.nf; ++i) {
                                 R.key[i] = FL.key[i];
-                                R.r2[i] = FL.r2[i];
+                                R.r[i] = FL.r[i];
+                                R.cd[i] = FL.cd[i];
                             }
                         }
                     }
@@ -498,7 +499,8 @@ __global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, S
                 }
                 for (int i = lane; i < T.nf; i += 32) {
                     R.key[i] = wr->key[i];
-                    R.r2[i] = wr->r2[i];
+                    R.r[i] = wr->r[i];
+                    R.cd[i] = wr->cd[i];
                 }
             }
             __syncwarp();  // the record is read before the next seed overwrites it
@@ -566,10 +568,7 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
                 int part = -1;
                 float r2 = P.lam;
                 for (int i = 0; i < R.nf; ++i)
-                    if ((int)(R.key[i] & 0xffffu) == w) {
-                        part = (int)(R.key[i] >> 16);
-                        r2 = R.r2[i];
-                    }
+                    if (key_wire(R.key[i]) == w) r2 = entry_class(R.key[i], R.r[i], R.cd[i], P.lam, part);
                 if (hit_part) hit_part[h] = (int8_t)part;
                 if (hit_res2) hit_res2[h] = r2;
             }
@@ -585,10 +584,7 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
         int part = -1;
         float r2 = P.lam;
         for (int i = 0; i < T.nf; ++i)
-            if ((int)(rec->key[i] & 0xffffu) == w) {
-                part = (int)(rec->key[i] >> 16);
-                r2 = rec->r2[i];
-            }
+            if (key_wire(rec->key[i]) == w) r2 = entry_class(rec->key[i], rec->r[i], rec->cd[i], P.lam, part);
         if (hit_part) hit_part[h] = (int8_t)part;
         if (hit_res2) hit_res2[h] = r2;
     }
@@ -846,6 +842,17 @@ __global__ void propagate_fp64_kernel(DevGeom G, DevField F, ScanConst P, int n_
 // ----------------------------------------------------------- launchers
 static int blocks_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
+// A timer mark on stream st: recorded at once, or, while st is being captured
+// into a CUDA graph, as an event-record node that every replay of the graph
+// records again.
+static void timer_mark(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 using ScanKernel = void (*)(DevGeom, DevField, ScanConst, ScanIO);
 
 template <int KIND>
@@ -895,7 +902,8 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                                                                                            L.zoom_grids);
         }
         float* E = (r == 0 && L.E0) ? L.E0 : W.E;
-        const long long cap = (r == 0 && L.E0) ? (1ll << 62) : W.e_cap;
+        long long cap = (r == 0 && L.E0) ? (1ll << 62) : W.e_cap;
+        if (r == 0 && L.e0_cap >= 0) cap = std::min(cap, L.e0_cap);
         prologue_kernel<<<1, 1024, 0, st>>>(ne, grids, gpe, cap, W.seg_cap, W.seed_off, W.seg_off, W.counters,
                                             L.flags);
         if (r == 0 && W.perm)
@@ -905,7 +913,7 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
                   L.steps ? L.steps + r : nullptr, r == 0 ? W.perm : nullptr, rec ? W.recs : nullptr,
                   W.rec_count, W.run_best, r};
         const bool timed = L.timer.ev && *L.timer.used + 2 <= L.timer.cap;
-        if (timed) cudaEventRecord(L.timer.ev[*L.timer.used], st);
+        if (timed) timer_mark(L.timer.ev[*L.timer.used], st);
         // a round of few seeds (host bound: zoom grids of 3^5 seeds) runs one warp per seed
         const long long round_seeds = (long long)ne * L.n_zoom * ZOOM_GRID;
         if (r > 0 && round_seeds <= L.warp_seeds) {
@@ -923,7 +931,7 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
             kern<<<nb, bs, 0, st>>>(G, F, P, io);
         }
         if (timed) {
-            cudaEventRecord(L.timer.ev[*L.timer.used + 1], st);
+            timer_mark(L.timer.ev[*L.timer.used + 1], st);
             *L.timer.used += 2;
         }
         // one warp per 4096-seed segment; a zoom round has at most round_seeds / SEG + ne segments

@@ -28,8 +28,9 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // A: states of seeds [s0, s0 + n) (global seed indices in row-major order):
 // rec_r[i * stride + j] = (x, y, z, partition), rec_t[...] = (tx, ty, tz, 0) after
-// step j (j = 0: the seed), n_rec[i] = steps taken, end_ok[i] = 1 if the track
-// did not end at the partition limit (its end may then be a minimum).
+// step j (j = 0: the seed), n_rec[i] = steps taken, end_ok[i] = 1 + the
+// partition of the end point if the track did not end at the partition limit
+// (its end may then be a minimum), else 0.
 template <int KIND>
 __global__ void __launch_bounds__(128) record_kernel(DevGeom G, DevField F, ScanConst P, const cdc_grid* grids,
                                                      const long long* seed_off, const unsigned long long* counters,
@@ -70,13 +71,15 @@ __global__ void __launch_bounds__(128) record_kernel(DevGeom G, DevField F, Scan
         rt[k] = make_float4(st.tx, st.ty, st.tz, 0.f);
     }
     n_rec[i] = k;
-    end_ok[i] = part < P.max_part ? 1 : 0;
+    end_ok[i] = part < P.max_part ? (int8_t)(part + 1) : (int8_t)0;
 }
 
 // B: Eq. 1 of seed i = one block; the recorded states are staged in shared
-// memory, then every thread takes hits of the seed's event: the smallest
-// squared residual of the hit's wire over all minima of the distance along the
-// track, capped at lambda.
+// memory, then every thread takes hits of the seed's event: per turn partition
+// the DCA of the hit's wire is the smallest distance over the partition's
+// minima, and the hit's term is the smallest min((DCA - drift)^2, lambda) over
+// the partitions (minima come in track order, so a partition's DCA is final
+// once a later partition's minimum appears).
 template <int KIND>
 __global__ void split_doca_kernel(DevGeom G, ScanConst P, const long long* seed_off, int n_events, long long s0,
                                   int stride, const float4* __restrict__ rec_r, const float4* __restrict__ rec_t,
@@ -99,7 +102,7 @@ __global__ void split_doca_kernel(DevGeom G, ScanConst P, const long long* seed_
     }
     for (int l = threadIdx.x; l < G.n_layers; l += blockDim.x) s_lay[l] = G.layers[l];
     __syncthreads();
-    const bool end_min = end_ok[i] != 0;
+    const int end_part = (int)end_ok[i] - 1;  // -1: the end is no minimum
     float acc = 0.f;
     for (int h = hit_off[ev] + threadIdx.x; h < hit_off[ev + 1]; h += blockDim.x) {
         const int w = wire_id[h];
@@ -115,30 +118,37 @@ __global__ void split_doca_kernel(DevGeom G, ScanConst P, const long long* seed_
         }
         const float cosa = s_lay[a].cosa;
         const float4 W = __ldg(G.wires + w);
-        float best = INFINITY, tp2;
+        float best = P.lam, dmin = INFINITY, tp2;  // best term of the finished partitions; DCA of partition cp
+        int cp = 0;
+        auto minimum = [&](int k, float D) {
+            if (k != cp) {
+                const float r = dmin - d;
+                best = fminf(best, fminf(r * r, P.lam));
+                cp = k;
+                dmin = D;
+            } else {
+                dmin = fminf(dmin, D);
+            }
+        };
         float4 r0 = sr[0], t0 = stt[0];
         float g0 = dist_slope(r0.x, r0.y, r0.z, t0.x, t0.y, t0.z, W, cosa, tp2);
-        if (g0 > 0.f) {  // the start of the track: a minimum if the distance grows from there
-            const float r = point_doca(r0.x, r0.y, r0.z, W, cosa) - d;
-            best = r * r;
-        }
+        // the start of the track: a minimum if the distance grows from there
+        if (g0 > 0.f) minimum(0, point_doca(r0.x, r0.y, r0.z, W, cosa));
         for (int j = 1; j <= n; ++j) {
             const float4 r1 = sr[j], t1 = stt[j];
             const float g1 = dist_slope(r1.x, r1.y, r1.z, t1.x, t1.y, t1.z, W, cosa, tp2);
-            if (g0 < 0.f && g1 >= 0.f) {
-                const float r = seg_doca(r0.x - W.x, r0.y - W.y, r0.z, t0.x, t0.y, t0.z, r1.x - r0.x, r1.y - r0.y,
-                                         r1.z - r0.z, t1.x, t1.y, t1.z, W, cosa, g0, g1, P.h) - d;
-                best = fminf(best, r * r);
-            }
+            if (g0 < 0.f && g1 >= 0.f)  // a segment belongs to the partition at its start
+                minimum(__float_as_int(r1.w), seg_doca(r0.x - W.x, r0.y - W.y, r0.z, t0.x, t0.y, t0.z, r1.x - r0.x,
+                                                       r1.y - r0.y, r1.z - r0.z, t1.x, t1.y, t1.z, W, cosa, g0, g1,
+                                                       P.h));
             r0 = r1;
             t0 = t1;
             g0 = g1;
         }
-        if (end_min && g0 < 0.f) {  // the end of the track, still approaching
-            const float r = point_doca(r0.x, r0.y, r0.z, W, cosa) - d;
-            best = fminf(best, r * r);
-        }
-        acc += fminf(best, P.lam);
+        // the end of the track, still approaching
+        if (end_part >= 0 && g0 < 0.f) minimum(end_part, point_doca(r0.x, r0.y, r0.z, W, cosa));
+        const float r = dmin - d;
+        acc += fminf(best, fminf(r * r, P.lam));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL_MASK, acc, o);
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;

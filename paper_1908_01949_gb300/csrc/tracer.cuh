@@ -26,9 +26,18 @@
 // still decreasing there.  If a list overflows, the tracer searches the window
 // at every step until the next rebuild.
 //
+// Eq. 1 per wire: the DCA of a turn partition is the smallest distance over
+// all minima inside that partition, and the wire's term is the smallest
+// min((|DCA_k| - drift)^2, lambda) over the partitions k.  A minimum closer than
+// drift - sqrt(lambda) therefore removes its partition from the wire's term,
+// and a minimum farther than drift + sqrt(lambda) never matters.  The record
+// keeps, per wire with a minimum closer than drift + sqrt(lambda), the signed
+// residual of the current partition's DCA and the best term of the earlier
+// partitions (minima arrive in track order, so partitions only grow).
+//
 // Layout: every scalar of the tracer lives in registers; the list lives in
-// shared memory ([LIST_CAP][block] layout), the per-seed record of wires scored
-// below lambda (written a few times per seed) in local memory.
+// shared memory ([LIST_CAP][block] layout), the per-seed record (written a few
+// times per seed) in local memory.
 #pragma once
 
 #include "cdc_dev.cuh"
@@ -38,11 +47,52 @@ namespace cdc {
 constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
-// Wires scored below lambda by one seed: wire | partition << 16, and res^2.
+// Record of one seed, one entry per wire that has a distance minimum closer
+// than drift + sqrt(lambda): key = wire | pc << 16 | pd << 20; r = DCA - drift
+// of partition pc so far (-inf once a minimum of pc is known to lie closer
+// than drift - sqrt(lambda)); cd = min(res^2, lambda) of the best earlier
+// partition pd (lambda: none).
 struct FoundList {
     uint32_t key[CDC_MAX_FOUND];
-    float r2[CDC_MAX_FOUND];
+    float r[CDC_MAX_FOUND];
+    float cd[CDC_MAX_FOUND];
 };
+
+__device__ __forceinline__ int key_wire(uint32_t k) { return (int)(k & 0xffffu); }
+__device__ __forceinline__ int key_pc(uint32_t k) { return (int)((k >> 16) & 0xfu); }
+__device__ __forceinline__ int key_pd(uint32_t k) { return (int)((k >> 20) & 0xfu); }
+
+// Eq. 1 term of a record entry: the best of the earlier partitions and the
+// current one.
+__device__ __forceinline__ float entry_term(float r, float cd, float lam) { return fminf(cd, fminf(r * r, lam)); }
+
+// A minimum of partition pt >= pc with signed residual r joins the entry:
+// within pc the DCA is the smaller distance; a later partition first folds
+// pc's term into (cd, pd).
+__device__ __forceinline__ void entry_merge(uint32_t& key, float& rc, float& cd, int pt, float r, float lam) {
+    const int pc = key_pc(key);
+    if (pt == pc) {
+        rc = fminf(rc, r);
+        return;
+    }
+    const float cc = fminf(rc * rc, lam);
+    if (cc < cd) {
+        cd = cc;
+        key = (key & ~(0xfu << 20)) | ((uint32_t)pc << 20);
+    }
+    key = (key & ~(0xfu << 16)) | ((uint32_t)pt << 16);
+    rc = r;
+}
+
+// Hit classification of a record entry (sec. 2.2: d^2 < lambda): the
+// partition of the smallest term, ties to the lower partition, or -1; returns
+// the term.
+__device__ __forceinline__ float entry_class(uint32_t key, float rc, float cd, float lam, int& part) {
+    const float cc = fminf(rc * rc, lam);
+    const float b = fminf(cd, cc);
+    part = b < lam ? (cd <= cc ? key_pd(key) : key_pc(key)) : -1;
+    return b;
+}
 
 // Fired cells of layer L in the search window (half widths band [mm] in
 // radius, given as the squared bounds blo2..bhi2, and d_win <= TAB_BAND [mm]
@@ -203,24 +253,26 @@ __device__ __forceinline__ bool in_chamber(const uchar2* s_tab, float rho) {
     return lr.x <= lr.y;
 }
 
-// Squared residual of the distance minimum to wire W inside the segment
-// o -> n (slopes g0 < 0 <= g1, drift d), or +inf where cheap bounds rule out
-// |D - d| < sqrt(lambda) (with 0.01 mm to spare): D <= min(D0, D1), and with
-// D^2' = 2 g and g' >= -kap |w_perp| (kap = |lam| b_max), D^2 >= D0^2 + 2 g0 h
-// - kap (D0 + h) h^2 and D^2 >= D1^2 - 2 g1 h - kap (D1 + h) h^2.
-__device__ __forceinline__ float seg_res2(const ScanConst& P, float kap, float ox, float oy, float oz, float otx,
-                                          float oty, float otz, float nx, float ny, float nz, float ntx, float nty,
-                                          float ntz, float4 W, float cosa, float d, float g0, float g1) {
+// Signed residual D - d of the distance minimum to wire W inside the segment
+// o -> n (slopes g0 < 0 <= g1, drift d), where cheap bounds do not settle it
+// (with 0.01 mm to spare): +inf when D > d + sqrt(lambda) (the minimum cannot
+// matter), -inf when D < d - sqrt(lambda) (it removes its partition from the
+// wire's term).  D <= min(D0, D1), and with D^2' = 2 g and g' >= -kap |w_perp|
+// (kap = |lam| b_max), D^2 >= D0^2 + 2 g0 h - kap (D0 + h) h^2 and
+// D^2 >= D1^2 - 2 g1 h - kap (D1 + h) h^2.
+__device__ __forceinline__ float seg_res(const ScanConst& P, float kap, float ox, float oy, float oz, float otx,
+                                         float oty, float otz, float nx, float ny, float nz, float ntx, float nty,
+                                         float ntz, float4 W, float cosa, float d, float g0, float g1) {
     const float h = P.h;
     const float D0s = point_doca2(ox, oy, oz, W, cosa), D1s = point_doca2(nx, ny, nz, W, cosa);
     const float kh2 = kap * h * h;
     const float lb2 = fmaxf(fmaf(2.0f * h, g0, fmaf(-kh2, sqrt_ub(D0s) + h, D0s)),
                             fmaf(-2.0f * h, g1, fmaf(-kh2, sqrt_ub(D1s) + h, D1s)));
     const float hi = d + P.sqrt_lam + 0.01f, lo = d - P.sqrt_lam - 0.01f;
-    if (lb2 > hi * hi || (lo > 0.f && fminf(D0s, D1s) < lo * lo)) return INFINITY;
-    const float r = seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W, cosa,
-                             g0, g1, h) - d;
-    return r * r;
+    if (lb2 > hi * hi) return INFINITY;
+    if (lo > 0.f && fminf(D0s, D1s) < lo * lo) return -INFINITY;
+    return seg_doca(ox - W.x, oy - W.y, oz, otx, oty, otz, nx - ox, ny - oy, nz - oz, ntx, nty, ntz, W, cosa, g0, g1,
+                    h) - d;
 }
 
 template <int KIND>
@@ -237,28 +289,33 @@ struct Tracer {
     unsigned long long bloom;
     uint32_t flags;
 
-    // Best squared residual of `wire` below lambda; Eq. 1 accumulates
-    // min(res^2, lambda) - lambda on top of H lambda.
-    __device__ __forceinline__ void found(const ScanConst& P, FoundList& FL, int wire, int pt, float r2) {
-        if (!(r2 < P.lam)) return;
+    // A distance minimum of `wire` in partition pt with signed residual r =
+    // D - drift; Eq. 1 accumulates the change of the wire's term on top of
+    // H lambda.  Minima with D >= drift + sqrt(lambda) never lower a term.
+    __device__ __forceinline__ void found(const ScanConst& P, FoundList& FL, int wire, int pt, float r) {
+        if (!(r < P.sqrt_lam)) return;
         const unsigned long long bit = 1ull << (wire & 63);
         if (bloom & bit) {
             for (int i = 0; i < nf; ++i) {
-                if ((int)(FL.key[i] & 0xffffu) == wire) {
-                    if (r2 < FL.r2[i]) {
-                        eacc += r2 - FL.r2[i];
-                        FL.r2[i] = r2;
-                        FL.key[i] = (uint32_t)wire | ((uint32_t)pt << 16);
-                    }
+                uint32_t k = FL.key[i];
+                if (key_wire(k) == wire) {
+                    float rc = FL.r[i], cd = FL.cd[i];
+                    const float old = entry_term(rc, cd, P.lam);
+                    entry_merge(k, rc, cd, pt, r, P.lam);
+                    eacc += entry_term(rc, cd, P.lam) - old;
+                    FL.key[i] = k;
+                    FL.r[i] = rc;
+                    FL.cd[i] = cd;
                     return;
                 }
             }
         }
         bloom |= bit;
-        eacc += r2 - P.lam;
+        eacc += fminf(r * r, P.lam) - P.lam;
         if (nf < CDC_MAX_FOUND) {
             FL.key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
-            FL.r2[nf] = r2;
+            FL.r[nf] = r;
+            FL.cd[nf] = P.lam;
             ++nf;
         } else {
             flags |= CDC_FLAG_FOUND_OVERFLOW;
@@ -342,10 +399,8 @@ struct Tracer {
                          [&](int wire, float d, float cosa) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
-                             if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f) {
-                                 const float r = point_doca(x, y, z, W, cosa) - d;
-                                 found(P, FL, wire, 0, r * r);
-                             }
+                             if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f)
+                                 found(P, FL, wire, 0, point_doca(x, y, z, W, cosa) - d);
                          });
         rebuild(G, P, s_lay, s_tab);
     }
@@ -374,8 +429,8 @@ struct Tracer {
             const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, tp2);
             if (e.y < 0.f && g1 >= 0.f)
                 found(P, FL, wire, part,
-                      seg_res2(P, kap, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, e.z, e.y,
-                               g1));
+                      seg_res(P, kap, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, e.z, e.y,
+                              g1));
             e.y = g1;
             cand[k * stride] = e;
         }
@@ -399,8 +454,8 @@ struct Tracer {
                              const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2);
                              if (g1 >= 0.f)
                                  found(P, FL, wire, pt,
-                                       seg_res2(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa,
-                                                d, g0, g1));
+                                       seg_res(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa,
+                                               d, g0, g1));
                          });
         }
         const bool now_out = rho >= G.R0;
@@ -424,10 +479,8 @@ struct Tracer {
                          [&](int wire, float d, float cosa) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
-                             if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
-                                 const float r = point_doca(nx, ny, nz, W, cosa) - d;
-                                 found(P, FL, wire, pe, r * r);
-                             }
+                             if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f)
+                                 found(P, FL, wire, pe, point_doca(nx, ny, nz, W, cosa) - d);
                          });
         }
         return !stop;

@@ -9,8 +9,8 @@
 //   - a window search takes one layer per lane, places the layers' fired
 //     wires by a warp prefix sum in the visiting order of visit_window (layer
 //     by layer, cell by cell) and hands one wire to each lane;
-//   - the record of wires scored below lambda lives in shared memory, where
-//     all lanes search it at once.
+//   - the record of the seed's wires (tracer.cuh: FoundList) lives in shared
+//     memory, where all lanes search it at once.
 // Minima are recorded in the same order as by Tracer, so both compute the
 // same Eq. 1 sums.
 #pragma once
@@ -23,11 +23,12 @@ constexpr unsigned WARP_ALL = 0xffffffffu;
 constexpr int WARP_LIST_CAP = 32;  // candidate wires per seed: one per lane
 constexpr int WIN_CAP = 128;       // fired wires of one window kept in shared memory
 
-// Per-warp shared memory: the record of the warp's seed (wire | partition <<
-// 16, and res^2) and the fired wires of the current window (wire | layer << 16).
+// Per-warp shared memory: the record of the warp's seed (the entries of
+// FoundList) and the fired wires of the current window (wire | layer << 16).
 struct WarpFound {
     uint32_t key[CDC_MAX_FOUND];
-    float r2[CDC_MAX_FOUND];
+    float r[CDC_MAX_FOUND];
+    float cd[CDC_MAX_FOUND];
     uint32_t win[WIN_CAP];
 };
 
@@ -136,33 +137,36 @@ struct WarpTracer {
         }
     }
 
-    // Best squared residual of `wire` below lambda (arguments equal on all
-    // lanes); Eq. 1 accumulates min(res^2, lambda) - lambda on top of H lambda.
-    __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r2) {
-        if (!(r2 < P.lam)) return;
+    // A distance minimum of `wire` in partition pt with signed residual r
+    // (arguments equal on all lanes): the rules of Tracer::found.
+    __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r) {
+        if (!(r < P.sqrt_lam)) return;
         for (int b = 0; b < nf; b += 32) {
             const int i = b + lane;
-            const unsigned m = __ballot_sync(WARP_ALL, i < nf && (int)(rec->key[i] & 0xffffu) == wire);
+            const unsigned m = __ballot_sync(WARP_ALL, i < nf && key_wire(rec->key[i]) == wire);
             if (m) {
                 const int k = b + __ffs(m) - 1;
-                const float old = rec->r2[k];
+                uint32_t key = rec->key[k];
+                float rc = rec->r[k], cd = rec->cd[k];
                 __syncwarp();
-                if (r2 < old) {
-                    eacc += r2 - old;
-                    if (lane == 0) {
-                        rec->r2[k] = r2;
-                        rec->key[k] = (uint32_t)wire | ((uint32_t)pt << 16);
-                    }
+                const float old = entry_term(rc, cd, P.lam);
+                entry_merge(key, rc, cd, pt, r, P.lam);
+                eacc += entry_term(rc, cd, P.lam) - old;
+                if (lane == 0) {
+                    rec->key[k] = key;
+                    rec->r[k] = rc;
+                    rec->cd[k] = cd;
                 }
                 __syncwarp();
                 return;
             }
         }
-        eacc += r2 - P.lam;
+        eacc += fminf(r * r, P.lam) - P.lam;
         if (nf < CDC_MAX_FOUND) {
             if (lane == 0) {
                 rec->key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
-                rec->r2[nf] = r2;
+                rec->r[nf] = r;
+                rec->cd[nf] = P.lam;
             }
             ++nf;
         } else {
@@ -171,13 +175,14 @@ struct WarpTracer {
         __syncwarp();
     }
 
-    // Minima found by the lanes (r2 = +inf where none), recorded in lane order.
-    __device__ __forceinline__ void record_lanes(const ScanConst& P, float r2, int wire, int pt) {
-        unsigned m = __ballot_sync(WARP_ALL, r2 < P.lam);
+    // Minima found by the lanes (signed residuals; +inf where none), recorded
+    // in lane order.
+    __device__ __forceinline__ void record_lanes(const ScanConst& P, float r, int wire, int pt) {
+        unsigned m = __ballot_sync(WARP_ALL, r < P.sqrt_lam);
         while (m) {
             const int src = __ffs(m) - 1;
             m &= m - 1;
-            found(P, __shfl_sync(WARP_ALL, wire, src), pt, __shfl_sync(WARP_ALL, r2, src));
+            found(P, __shfl_sync(WARP_ALL, wire, src), pt, __shfl_sync(WARP_ALL, r, src));
         }
     }
 
@@ -267,19 +272,16 @@ struct WarpTracer {
                 int wire;
                 float cosa;
                 window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, z, tot, pass * 32 + lane, wire, cosa);
-                float r2 = INFINITY;
+                float r = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
                     if (d <= P.max_drift) {
                         const float4 W = __ldg(G.wires + wire);
                         float tp2;
-                        if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f) {
-                            const float r = point_doca(x, y, z, W, cosa) - d;
-                            r2 = r * r;
-                        }
+                        if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f) r = point_doca(x, y, z, W, cosa) - d;
                     }
                 }
-                record_lanes(P, r2, wire, 0);
+                record_lanes(P, r, wire, 0);
             }
         }
         rebuild(G, P, s_lay, s_tab);
@@ -299,17 +301,17 @@ struct WarpTracer {
     // Sign tests of the listed wires, one per lane.
     __device__ __forceinline__ void list_pass(const DevGeom& G, const ScanConst& P) {
         if (over) return;
-        float r2 = INFINITY;
+        float r = INFINITY;
         if (lane < nc) {
             const float4 W = c_W;
             float tp2;
             const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, c_cosa, tp2);
             if (c_g < 0.f && g1 >= 0.f)
-                r2 = seg_res2(P, fabsf(s.lam) * P.b_max, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty,
-                              s.tz, W, c_cosa, c_d, c_g, g1);
+                r = seg_res(P, fabsf(s.lam) * P.b_max, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz,
+                            W, c_cosa, c_d, c_g, g1);
             c_g = g1;
         }
-        record_lanes(P, r2, c_wire, part);
+        record_lanes(P, r, c_wire, part);
     }
 
     // Window search when the list overflowed, turn bookkeeping, stop tests and
@@ -326,7 +328,7 @@ struct WarpTracer {
                 int wire;
                 float cosa;
                 window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, nz, tot, pass * 32 + lane, wire, cosa);
-                float r2 = INFINITY;
+                float r = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
                     if (d <= P.max_drift) {
@@ -336,12 +338,12 @@ struct WarpTracer {
                         if (g0 < 0.f) {
                             const float g1 = dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2);
                             if (g1 >= 0.f)
-                                r2 = seg_res2(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa, d,
-                                              g0, g1);
+                                r = seg_res(P, kap, ox, oy, oz, otx, oty, otz, nx, ny, nz, ntx, nty, ntz, W, cosa, d,
+                                            g0, g1);
                         }
                     }
                 }
-                record_lanes(P, r2, wire, part);
+                record_lanes(P, r, wire, part);
             }
         }
         const bool now_out = rho >= G.R0;
@@ -363,19 +365,17 @@ struct WarpTracer {
                 int wire;
                 float cosa;
                 window_entry(s_lay, s_tab, P.band, P.d_win, rho, phi, nz, tot, pass * 32 + lane, wire, cosa);
-                float r2 = INFINITY;
+                float r = INFINITY;
                 if (wire >= 0) {
                     const float d = __ldg(dtab + wire);
                     if (d <= P.max_drift) {
                         const float4 W = __ldg(G.wires + wire);
                         float tp2;
-                        if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f) {
-                            const float r = point_doca(nx, ny, nz, W, cosa) - d;
-                            r2 = r * r;
-                        }
+                        if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f)
+                            r = point_doca(nx, ny, nz, W, cosa) - d;
                     }
                 }
-                record_lanes(P, r2, wire, part);
+                record_lanes(P, r, wire, part);
             }
         }
         return !stop;

@@ -1,6 +1,6 @@
 """GPU behaviour at the scan's limits, against the FP64 oracle: the step cap,
-the largest top-K list, and a seed that scores more wires below lambda than
-its record holds."""
+the largest top-K list, and a seed that scores more wires than its record
+holds."""
 import numpy as np
 import pytest
 
@@ -8,7 +8,7 @@ import cdc_synth as S
 import oracle as O
 from tests.gpu_util import check_topk, compare_scores, keys_to_index, oracle_params, tracker
 
-CDC_MAX_FOUND = 128   # wires a seed's record holds (include/cdc.h)
+CDC_MAX_FOUND = 128   # record entries of a seed (include/cdc.h)
 
 pytestmark = pytest.mark.gpu
 
@@ -59,8 +59,9 @@ def test_largest_top_k_matches_oracle():
 
 def test_record_overflow_is_flagged():
     """Three turns of 137 signal hits at lambda = 9 mm^2: seeds near the truth
-    score 133-137 wires below lambda, more than the 128 their record holds, and
-    the event carries the overflow flag; followed over one turn only (under 128
+    score 133-137 wires below lambda, more than the 128 entries their record
+    holds (one per wire with a pass closer than drift + sqrt(lambda)), and the
+    event carries the overflow flag; followed over one turn only (about 65 such
     wires) the same seeds raise no flag and score like the oracle."""
     import paper_1908_01949_gb300 as cdc
     fm = S.solenoid_map()

@@ -79,3 +79,52 @@ def test_noalloc_scan_rejects_sizes_beyond_its_array():
     with pytest.raises(cdc.CdcError, match="n_rounds"):
         tr.ctx.cdc_scan_seeds_noalloc(1, 10, off, wid, dr, dg, cdc.scan_params(k=8, n_rounds=2), None, None, be, bs,
                                       None, None, fl, None)
+
+
+def test_noalloc_scan_without_E_and_grids_beyond_the_stated_count():
+    """Without E the scores stay in the library's array: top-K, best seeds and
+    hit classes still equal the reserved scan's.  A second call takes no
+    device memory.  Grids holding more seeds than the caller states scan
+    nothing and flag the event empty, with or without E, and leave E as it
+    was."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    from tests.gpu_util import tracker
+    g, f, ev, grid = S.cfg1_case(10)
+    n = int(np.prod(grid["n"][0]))
+    tr = tracker(g, f)
+    ref, _ = _run_both(tr, ev, grid, 4.0)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    dg = cdc.grids_to_tensor(grid, tr.dev)
+    p = cdc.scan_params(h=2.0, max_steps=1000, lam=4.0, max_partitions=1, k=8, n_rounds=1)
+    t = torch
+    out = dict(topk0=t.empty((1, 8), dtype=t.int64, device=tr.dev),
+               best_E=t.empty((1, 8), dtype=t.float32, device=tr.dev),
+               best_seed=t.empty((1, 8, 5), dtype=t.float32, device=tr.dev),
+               hit_part=t.empty(ev.wire_id.size, dtype=t.int8, device=tr.dev),
+               hit_res2=t.empty(ev.wire_id.size, dtype=t.float32, device=tr.dev),
+               flags=t.empty(1, dtype=t.int32, device=tr.dev), steps=t.zeros(1, dtype=t.int64, device=tr.dev))
+
+    def call(n_stated, E=None):
+        out["steps"].zero_()                  # the call adds its step count to the counter
+        tr.ctx.cdc_scan_seeds_noalloc(1, n_stated, off, wid, dr, dg, p, E, out["topk0"], out["best_E"],
+                                      out["best_seed"], out["hit_part"], out["hit_res2"], out["flags"], out["steps"])
+
+    call(n)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(tr.dev)[0]
+    call(n)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(tr.dev)[0] == free0
+    for key in ("topk0", "best_E", "best_seed", "hit_part", "hit_res2", "flags"):
+        assert torch.equal(out[key], ref[key]), key
+    assert int(out["steps"][0]) == int(ref["steps"][0])
+    for with_E in (False, True):
+        E = torch.full((n,), -1.0, dtype=torch.float32, device=tr.dev) if with_E else None
+        call(n - 1, E)
+        torch.cuda.synchronize()
+        assert int(out["flags"][0]) & cdc.FLAG_EMPTY
+        assert int(out["steps"][0]) == 0
+        assert np.all(np.isinf(out["best_E"].cpu().numpy()))
+        if with_E:
+            assert torch.all(E == -1.0)
