@@ -1,35 +1,35 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 seed-scanning track finder.
 
-Workload (one step = one event, the single-event multi-turn configuration):
-a 104.97 MeV/c e- making 2-3 turns in a finite-solenoid field map (451 x 1001
-samples at 2 mm), 10 % wire occupancy of DIO-like noise (e- uniform in 40-100
-MeV/c); circle Hough (512 x 512 int32) -> a 10^6-seed grid around the top
-peak (10 theta0 x 40 z0 x 10 px0 x 10 py0 x 25 pz0) -> ten scan rounds (the
+Headline (one step = one CUDA-graph replay of the batched configuration):
+256 events, each a 104.97 MeV/c e- of 1-3 turns with 30-200 hits in the
+finite-solenoid field map (451 x 1001 samples at 2 mm) plus DIO-like noise at
+an occupancy uniform in 5-20 %, each with a seed grid of log-uniform 10^4-10^6
+seeds around its first turn (~5.7e7 coarse seeds); ten scan rounds (the
 coarse grid plus nine zoom rounds of 4 x 3^5 seeds at halved steps) with up to
-3500 RKN steps of 2 mm and 3 turn partitions -> hit classification of the best
-seed.  Inputs are seeded synthetic events generated on the host.
+3500 RKN steps of 2 mm and 3 turn partitions, and the hit classification of
+every event's best seed, all in one CUDA graph.  value = seeds/s (coarse and
+zoom seeds of all events over the replay's CUDA-event time); the roofline is
+the coarse-round scan launch inside the graph against the FP32 FMA throughput
+measured on the same GPU.  Inputs are seeded synthetic events generated on
+the host.
 
-Refine leg (timed separately, reported beside the scan): the 64 best seeds of
-each of 16 such events (one ten-round scan with k = 64 each) placed in 1024
-event slots (65536 seeds), five Gauss-Newton iterations with forward tangents,
-checkpointed adjoint gradient and the FP64 5x5 solve.
+Legs (timed separately, reported beside the headline):
+  multi_turn: the single-event multi-turn configuration (circle Hough
+    512 x 512 int32 -> a 10^6-seed grid -> ten rounds -> classification),
+    eight distinct events in flight, and its one-event latency;
+  single_turn: the uniform-field single-turn configuration (4000 seeds);
+  refine: the 64 best seeds of each of 1024 distinct 3-turn events (65536
+    seeds), five Gauss-Newton iterations, checkpointed adjoint gradient;
+  sweep: 64 events at 30 % occupancy with 10^7 seeds in one CUDA graph, the
+    batched Hough, and the FP32 steppers against the FP64 GPU stepper to 6 m;
+  bidirectional, split_ab, event_loop: the ranked extensions.
 
-Batched leg (timed separately): 256 events with 1-3 turn signals of 30-200
-hits, 5-20 % DIO-like occupancy and log-uniform 10^4-10^6 seeds per event,
-all ten rounds of all events in one CUDA-graph replay per step.
-
-Sweep leg (timed separately): 64 events at 30 % occupancy with 10^7 seeds in
-one CUDA graph; the batched Hough of all 64 events; and the FP32 scan and
-refine steppers against the FP64 GPU stepper at every 0.5 m up to 6 m on a
-10^4-seed subsample (the FP64 GPU stepper itself is tested against the FP64
-oracle).
-
---profile-case shrinks the coarse grid to 240000 seeds (6 pz0 values) for
+--profile-case runs only the multi-turn leg on a 240000-seed coarse grid for
 profiler captures; its line is marked as such and is not a benchmark result.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
-a bounded sample of the same workload instead.
+a bounded sample of the headline workload instead.
 """
 from __future__ import annotations
 
@@ -49,20 +49,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "seeds/s and RKN steps/s at 1 GB300 (frac. of FP32 peak) vs FP64 CPU oracle; refine seeds/s"
-WORKLOAD = ("single multi-turn 104.97 MeV e- event, solenoid map 451x1001 @ 2 mm, 10% DIO-like occupancy; "
-            "circle Hough 512x512 -> 10^6-seed grid (10 theta0 x 40 z0 x 10 px0 x 10 py0 x 25 pz0); "
-            "10 scan rounds (coarse + 9 zoom x 4 x 3^5); RKN h=2 mm, <=3500 steps, 3 partitions; "
-            "hit classification of the best seed")
+WORKLOAD = ("batched scan: 256 events in one CUDA-graph replay per step; per event a 104.97 MeV/c e- of 1-3 turns "
+            "(30-200 hits) plus 5-20 % DIO-like occupancy in the solenoid map 451x1001 @ 2 mm, and a seed grid of "
+            "log-uniform 10^4-10^6 seeds around its first turn (~5.7e7 coarse seeds in all); 10 scan rounds "
+            "(coarse + 9 zoom x 4 x 3^5), RKN h=2 mm, <=3500 steps, 3 partitions; hit classification of every "
+            "event's best seed")
+WORKLOAD_MULTI_TURN = ("single multi-turn 104.97 MeV e- event, solenoid map 451x1001 @ 2 mm, 10% DIO-like occupancy; "
+                       "circle Hough 512x512 -> 10^6-seed grid (10 theta0 x 40 z0 x 10 px0 x 10 py0 x 25 pz0); "
+                       "10 scan rounds (coarse + 9 zoom x 4 x 3^5); RKN h=2 mm, <=3500 steps, 3 partitions; "
+                       "hit classification of the best seed")
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
 SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune_scan's timings
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch, from one
-# single-pass ncu capture of this benchmark's own launch (--scan-shape 256,16); valid only for the
-# kernel sources it was taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
-TRAFFIC = {"bytes": 34_728_448 + 16_658_176, "shape": "256x16", "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the coarse-round scan launch of each workload
+# from one single-pass ncu capture of this benchmark's own launch; valid only for the kernel sources it was
+# taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
+TRAFFIC = {
+    "batched": {"bytes": None, "shape": None, "csrc_sha256": None},
+    "multi_turn": {"bytes": None, "shape": None, "csrc_sha256": None},
+}
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 281.4, "fma_pipe_active_pct": 36.6, "csrc_sha256": "1975bb4b974f4f84665a5649ab7c1ec41a28361b9e7b305966e77b7d164bae96"}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": None, "fma_pipe_active_pct": None, "csrc_sha256": None}
+FFMA_ITERS = 4096                # iterations of the FP32 throughput kernel (~4 ms on a GB300)
 
 
 def csrc_digest() -> str:
@@ -93,6 +102,11 @@ def csrc_digest() -> str:
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()
+
+
+def recorded(entry):
+    """A recorded ncu figure if it was taken on the current kernel sources, else None."""
+    return entry if entry and entry.get("csrc_sha256") == csrc_digest() else None
 
 
 H, MAX_STEPS, LAM, MAX_PART, K, N_ROUNDS, N_ZOOM, MAX_DRIFT = 2.0, 3500, 4.0, 3, 8, 10, 4, 8.0
@@ -310,10 +324,59 @@ def time_graph(graph, out, flush, reps):
     return statistics.median(times), int(out["steps"].sum())
 
 
-def batched_leg(args, rank, local, g, fm, flush):
-    """Seeds/s of the batched workload: one CUDA graph holds the whole call
+
+def fp32_peak(tr, sampler):
+    """Measured FP32 FMA throughput of this GPU (cdc_fp32_peak: every SM at full
+    occupancy, eight independent FMA chains per thread), best of three
+    launches, with the SM clock sampled meanwhile; and the figure the unit
+    counts and the maximum clock give, for reference."""
+    import torch
+    tr.ctx.cdc_fp32_peak(256)                                     # warm-up (clock ramp)
+    sampler.start()
+    runs = [tr.ctx.cdc_fp32_peak(FFMA_ITERS) for _ in range(3)]
+    clocks = sampler.stop()
+    best = max(runs, key=lambda r: r[0])
+    props = torch.cuda.get_device_properties(tr.dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    units = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    return {"tflops": best[0], "ms": best[1], "runs_tflops": [r[0] for r in runs], "clocks": clocks,
+            "units_tflops": units,
+            "units_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                           f"{sm_max:.0f} MHz",
+            "kernel": "cdc_fp32_peak: 8 independent FFMA chains per thread x 16 x "
+                      f"{FFMA_ITERS} iterations, full occupancy on every SM, CUDA-event timed, best of 3"}
+
+
+def roofline(kernel, steps, ms, peak, traffic_key, shape):
+    """ALU roofline of a coarse-round scan launch: 198 algorithmic FP32
+    operations (FMA = 2) per executed RKN step over the launch's CUDA-event
+    time, against the measured FP32 FMA throughput."""
+    f_step = flops_per_step(1)
+    achieved = f_step * steps / (ms / 1e3) / 1e12
+    tr = recorded(TRAFFIC.get(traffic_key))
+    fc = recorded(FP32_COUNTS)
+    executed = fc["fp32_ops_per_rkn_step"] * steps / (ms / 1e3) / 1e12 if fc else None
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peak["tflops"], "traffic": tr["bytes"] if tr else None,
+            "peak_basis": "measured on this GPU in this run (cdc_fp32_peak, FFMA throughput)",
+            "peak_units": peak["units_tflops"], "frac_of_units": achieved / peak["units_tflops"],
+            "launch_ms": ms, "rkn_steps": steps, "flops_per_rkn_step": f_step,
+            "traffic_note": (f"DRAM bytes of this launch from one ncu capture at launch shape {tr['shape']} "
+                             f"(this run's shape {shape[0]}x{shape[1]}; the shapes run the same per-seed code)")
+                            if tr else "no ncu capture of the current kernel sources",
+            "ncu_fp32": ({"fp32_ops_per_rkn_step": fc["fp32_ops_per_rkn_step"],
+                          "fma_pipe_active_pct_240k_case": fc["fma_pipe_active_pct"],
+                          "executed_tflops": executed, "executed_fp32_frac_of_peak": executed / peak["tflops"],
+                          "note": "all executed FP32 work (FFMA = 2) per RKN step from ncu, times this launch's "
+                                  "steps over its CUDA-event time"} if fc else None)}
+
+
+def headline_batched(args, ws, rank, local, dist, g, fm, flush, sampler, peak):
+    """The batched configuration as the benchmark's step: the whole call
     (staging, ten rounds with their top-K and zoom grids, classification of
-    every event's best seed) and is replayed once per step."""
+    every event's best seed) in one CUDA graph, replayed once per step.  The
+    library's kernel timer marks the scan launches inside the graph, so the
+    coarse round's own CUDA-event time is read after every replay."""
     import torch
     import paper_1908_01949_gb300 as cdc
     n_ev = int(args.batched_events)
@@ -322,33 +385,325 @@ def batched_leg(args, rank, local, g, fm, flush):
     n = sum(counts)
     off, wid, dr = S.pack_events(evs)
     tr = cdc.Tracker(g, fm, device=local, max_events=n_ev, max_seeds=n, max_hits=int(wid.size))
+    dev = tr.dev
     sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
-    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
-    gr_t = cdc.grids_to_tensor(grids, tr.dev)
+    off_h = torch.from_numpy(off.astype(np.int32)).pin_memory()
+    wid_h = torch.from_numpy(wid.astype(np.int32)).pin_memory()
+    dr_h = torch.from_numpy(dr.astype(np.float32)).pin_memory()
+    gr_h = cdc.grids_to_tensor(grids, "cpu").pin_memory()
+    off_t, wid_t, dr_t, gr_t = (x.to(dev) for x in (off_h, wid_h, dr_h, gr_h))
     n_tune = min(n_ev, 32)    # tune on the first 32 events (one coarse round per shape)
-    tuned, tune_ms = tr.tune(off_t[:n_tune + 1], wid_t, dr_t, gr_t[:n_tune], sp, reps=1)
-    graph, out = graph_scan(tr, off_t, wid_t, dr_t, gr_t, sp, args.warmup)
-    ms, steps = time_graph(graph, out, flush, args.batched_steps)
+    if args.scan_shape:
+        tuned, tune_ms = tuple(int(x) for x in args.scan_shape.split(",")), None
+        tr.ctx.cdc_set_scan_config(*tuned)
+    else:
+        tuned, tune_ms = tr.tune(off_t[:n_tune + 1], wid_t, dr_t, gr_t[:n_tune], sp, reps=1)
+    # capture: eager warm call, then the graph with the kernel timer's marks as graph nodes
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
+    side.synchronize()
+    tr.ctx.cdc_kernel_timer(2)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        out = tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True, stream=side)
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
     seeds_step = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
+    # launches of this repository's kernels per replay (ncu launch list): staging 2, block order 1; per round
+    # prologue, scan, top-K partial and merge, best merge (5); a zoom-grid build per zoom round; assignment 1
+    launches_per_step = 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
+
+    def run():
+        times, coarse, steps = [], [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            try:
+                _, nl, per = tr.ctx.cdc_kernel_time()
+                coarse.append(float(per[0]) if nl else float("nan"))
+            except cdc.CdcError:
+                coarse.append(float("nan"))
+            steps.append(out["steps"].cpu().numpy().astype(np.float64))
+        return times, coarse, steps
+
+    (times, coarse, steps), clocks = timed_region(run, sampler, torch.cuda.synchronize, dist, dev)
+    ms = reduce_max(sum(times) / len(times), dist, dev)
+    rkn_step = float(np.mean([s.sum() for s in steps]))
+    coarse_steps = float(np.mean([s[0] for s in steps]))
+    coarse_ms = float(np.mean(coarse))
+    coarse_source = "event-record nodes around the coarse scan launch inside every timed replay"
+    if not np.isfinite(coarse_ms):
+        # the graph's timer nodes gave no time: the same call eager, marks around its coarse launch
+        tr.ctx.cdc_kernel_timer(1)
+        flush.zero_()
+        tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True)
+        _, nl, per = tr.ctx.cdc_kernel_time()
+        tr.ctx.cdc_kernel_timer(0)
+        coarse_ms = float(per[0])
+        coarse_source = "CUDA events around the coarse scan launch of one eager call of the same step"
     fl = out["flags"].cpu().numpy()
-    # classification quality (sec. 3.1, Eqs. 2-3): the grids are centred on the first turn, so
-    # scan partition k is truth turn k
-    truth = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=tr.dev)
+    # end to end: per step the events' hits and grids copied from pinned host memory into the graph's inputs,
+    # the replay, and every event's best seeds and scores, hit classes and flags copied back; host wall clock
+    k_e2e = max(1, min(args.steps, args.e2e_steps))
+    res = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory()
+           for k in ("best_E", "best_seed", "hit_part", "flags")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        for h, d in ((off_h, off_t), (wid_h, wid_t), (dr_h, dr_t), (gr_h, gr_t)):
+            d.copy_(h, non_blocking=True)
+        graph.replay()
+        for k, h in res.items():
+            h.copy_(out[k], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
+    h2d = int(sum(x.numel() * x.element_size() for x in (off_h, wid_h, dr_h, gr_h)))
+    d2h = int(sum(x.numel() * x.element_size() for x in res.values()))
+    # classification quality (sec. 3.1, Eqs. 2-3): the grids are centred on the first turn, so scan partition k
+    # is truth turn k
+    truth = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=dev)
     cls_counts = tr.classification_counts(off_t, out["hit_part"], truth, MAX_PART).cpu().numpy()
     eps, pur = cdc.efficiency_purity(cls_counts)
-    return {"events": n_ev, "coarse_seeds": n, "seeds_per_step": seeds_step,
-            "classification": {"partition": list(range(MAX_PART)),
-                               "efficiency": [None if np.isnan(x) else float(x) for x in eps],
-                               "purity": [None if np.isnan(x) else float(x) for x in pur],
-                               "definition": "Eqs. 2-3 summed over the events; scan partition k = truth turn k"},
-            "coarse_seeds_min_max": [min(counts), max(counts)], "hits": int(wid.size), "ms_per_step": ms,
-            "seeds_per_s": seeds_step / (ms / 1e3), "rkn_steps_per_s": steps / (ms / 1e3),
-            "events_per_s": n_ev / (ms / 1e3), "graph": "one CUDA graph per step (all rounds, all events)",
-            "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]}, "ms_by_shape": tune_ms,
-                         "events": n_tune},
-            "flagged_events": int((fl != 0).sum()), "timing": f"median of {args.batched_steps} graph replays, "
-                                                              "L2 flushed before each"}
+    return {
+        "ms": ms, "seeds_step": seeds_step, "rkn_step": rkn_step, "clocks": clocks, "n_events": n_ev,
+        "launches_per_step": launches_per_step,
+        "roofline": roofline("scan_kernel<map> (coarse round of the batched step, inside the graph)", coarse_steps,
+                             coarse_ms, peak, "batched", tuned),
+        "e2e": {"value": job_value(ws, seeds_step, e2e_ms), "unit": "seeds/s", "ms_per_step": e2e_ms,
+                "steps": k_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "detail": {"events": n_ev, "coarse_seeds": n, "seeds_per_step": seeds_step,
+                   "coarse_seeds_min_max": [min(counts), max(counts)], "hits": int(wid.size),
+                   "events_per_s": job_value(ws, n_ev, ms), "coarse_launch_ms": coarse_ms,
+                   "coarse_launch_timing": coarse_source,
+                   "replay_ms": times, "graph": "one CUDA graph per step (all rounds, all events)",
+                   "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]}, "ms_by_shape": tune_ms,
+                                "events": n_tune},
+                   "flagged_events": int((fl != 0).sum()),
+                   "classification": {"partition": list(range(MAX_PART)),
+                                      "efficiency": [None if np.isnan(x) else float(x) for x in eps],
+                                      "purity": [None if np.isnan(x) else float(x) for x in pur],
+                                      "definition": "Eqs. 2-3 summed over the events; scan partition k = truth "
+                                                    "turn k"}},
+        "workload": {"evs": evs, "grids": grids, "counts": counts},
+    }
+
+
+def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
+    """The single-event multi-turn configuration: circle Hough -> 10^6-seed grid
+    -> ten rounds -> classification of the best seed per event.  Throughput:
+    a stream of events with `inflight` of them in flight (one context and
+    stream each, each slot its own distinct event); latency and the coarse
+    round's roofline: one event at a time on one stream."""
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    dev = torch.device("cuda", local)
+    n_in = max(1, int(args.inflight))
+    evs = [S.cfg2_case(1000 * rank + k, fm, occupancy=0.10)[2] for k in range(n_in)]
+    tmpl = S.cfg2_grid_template()
+    if args.profile_case:
+        tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
+    seeds_coarse = int(np.prod(tmpl["n"][0]))
+    seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
+    hp = cdc.hough_params(grid_template=tmpl)
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
+                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    ne = 1
+
+    def make_slot(k):
+        """One event in flight: its own context (workspace), stream, event and buffers."""
+        ev = evs[k]
+        nh = int(ev.wire_id.size)
+        t = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
+        d = dict(tr=t, ctx=t.ctx, stream=torch.cuda.current_stream() if k == 0 else torch.cuda.Stream(device=dev),
+                 off_h=torch.tensor([0, nh], dtype=torch.int32).pin_memory(),
+                 wid_h=torch.from_numpy(ev.wire_id.astype(np.int32)).pin_memory(),
+                 dr_h=torch.from_numpy(ev.drift.astype(np.float32)).pin_memory(),
+                 acc=torch.empty((ne, hp.n_bins, hp.n_bins), dtype=torch.int32, device=dev),
+                 cand=torch.empty((ne, hp.max_cand, 28), dtype=torch.uint8, device=dev),
+                 ncand=torch.empty(ne, dtype=torch.int32, device=dev),
+                 grid=torch.empty((ne, cdc.GRID_BYTES), dtype=torch.uint8, device=dev),
+                 hflags=torch.empty(ne, dtype=torch.int32, device=dev),
+                 best_E=torch.empty((ne, K), dtype=torch.float32, device=dev),
+                 best_seed=torch.empty((ne, K, 5), dtype=torch.float32, device=dev),
+                 topk0=torch.empty((ne, K), dtype=torch.int64, device=dev),
+                 hit_part=torch.empty(nh, dtype=torch.int8, device=dev),
+                 sflags=torch.empty(ne, dtype=torch.int32, device=dev),
+                 steps=torch.zeros(N_ROUNDS, dtype=torch.int64, device=dev),
+                 out_E=torch.empty((ne, K), dtype=torch.float32).pin_memory(),
+                 out_S=torch.empty((ne, K, 5), dtype=torch.float32).pin_memory(),
+                 out_P=torch.empty(nh, dtype=torch.int8).pin_memory(),
+                 out_F=torch.empty(ne, dtype=torch.int32).pin_memory())
+        for a in ("off", "wid", "dr"):
+            d[a] = d[a + "_h"].to(dev)
+        return d
+
+    slots = [make_slot(k) for k in range(n_in)]
+    q0 = slots[0]
+    tr, ctx, stream = q0["tr"], q0["ctx"], q0["stream"]
+
+    def step(q, h2d=False, d2h=False):
+        """One event through the hot path on slot q's stream; with h2d / d2h the
+        inputs come from pinned host memory and the results go back to it."""
+        st = q["stream"]
+        with torch.cuda.stream(st):
+            if h2d:
+                for a in ("off", "wid", "dr"):
+                    q[a].copy_(q[a + "_h"], non_blocking=True)
+            q["ctx"].cdc_hough_seeds(ne, q["off"], q["wid"], hp, q["acc"], q["cand"], q["ncand"], q["grid"],
+                                     q["hflags"], st)
+            q["ctx"].cdc_scan_seeds(ne, q["off"], q["wid"], q["dr"], q["grid"], sp, None, q["topk0"], q["best_E"],
+                                    q["best_seed"], q["hit_part"], None, None, q["sflags"], q["steps"], st)
+            if d2h:
+                q["out_E"].copy_(q["best_E"], non_blocking=True)
+                q["out_S"].copy_(q["best_seed"], non_blocking=True)
+                q["out_P"].copy_(q["hit_part"], non_blocking=True)
+                q["out_F"].copy_(q["sflags"], non_blocking=True)
+
+    grid_for_tuning(ctx, ne, q0["off"], q0["wid"], hp, q0["acc"], q0["cand"], q0["ncand"], q0["grid"], q0["hflags"],
+                    stream)
+    if args.scan_shape:
+        tuned = tuple(int(x) for x in args.scan_shape.split(","))
+        tune_ms = None
+    else:
+        tuned, tune_ms = tr.tune(q0["off"], q0["wid"], q0["dr"], q0["grid"], sp, reps=3, stream=stream)
+    # zoom rounds (972 seeds per event): one event at a time, one warp per seed
+    # shortens them (latency); with many events in flight one lane per seed
+    # leaves the other events' coarse rounds the warp slots (throughput)
+    lat_ws = args.warp_seeds if args.warp_seeds is not None else ctx.cdc_get_scan_config()[2]
+    thr_ws = args.stream_warp_seeds
+    for q in slots:
+        q["ctx"].cdc_set_scan_config(*tuned, thr_ws)
+    ctx.cdc_set_scan_config(*tuned, lat_ws)
+    # Hough vote + peaks; table clear + staging; block order of the coarse grid; per round prologue, scan,
+    # top-K partial + merge, best merge; a zoom grid build per zoom round; hit assignment
+    launches_per_step = 2 + 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
+    for i in range(args.warmup * n_in):
+        step(slots[i % n_in])
+    torch.cuda.synchronize()
+
+    # latency and the roofline: one event at a time on one stream, the library's
+    # CUDA events around every scan-kernel launch
+    q0["steps"].zero_()
+    ctx.cdc_kernel_timer(True)
+    lat_ms = []
+    for i in range(args.mt_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(q0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat_ms.append(e0.elapsed_time(e1))
+    _, _, kper = ctx.cdc_kernel_time()
+    ctx.cdc_kernel_timer(False)
+    ctx.cdc_set_scan_config(*tuned, thr_ws)
+    rkn = q0["steps"].cpu().numpy().astype(np.float64)
+    coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
+    coarse_steps = float(rkn[0]) / args.mt_steps
+    latency = statistics.median(lat_ms)
+
+    # throughput: a stream of events, n_in of them in flight (one context and
+    # stream each, round robin); every step is one event's whole hot path
+    def run_stream(h2d=False, d2h=False):
+        main = torch.cuda.current_stream()
+        for q in slots:
+            q["steps"].zero_()
+            q["stream"].wait_stream(main)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(main)
+        for i in range(args.mt_steps):
+            q = slots[i % n_in]
+            with torch.cuda.stream(q["stream"]):
+                flush.zero_()
+            step(q, h2d, d2h)
+        for q in slots:
+            main.wait_stream(q["stream"])
+        e1.record(main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3
+
+    dev_ms, _ = run_stream()
+    ms = dev_ms / args.mt_steps
+    rkn_per_step = float(sum(q["steps"].sum().item() for q in slots)) / args.mt_steps
+    _, e2e_wall = run_stream(h2d=True, d2h=True)
+    e2e = e2e_wall / args.mt_steps
+    h2d = int(np.mean([sum(q[a + "_h"].numel() * 4 for a in ("off", "wid", "dr")) for q in slots]))
+    d2h = int(np.mean([q["out_E"].numel() * 4 + q["out_S"].numel() * 4 + q["out_P"].numel() + q["out_F"].numel() * 4
+                       for q in slots]))
+    return {
+        "workload": WORKLOAD_MULTI_TURN, "seeds_per_step": seeds_per_step, "ms_per_step": ms,
+        "seeds_per_s": job_value(ws, seeds_per_step, ms), "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
+        "events_in_flight": n_in, "distinct_events": n_in, "steps": args.mt_steps,
+        "zoom_rounds": {"throughput_run": "warp per seed" if thr_ws >= N_ZOOM * 243 else "lane per seed",
+                        "latency_run": "warp per seed" if lat_ws >= N_ZOOM * 243 else "lane per seed"},
+        "latency_ms_per_event": latency,
+        "roofline": roofline("scan_kernel<map> (coarse round of one event)", coarse_steps,
+                             statistics.mean(coarse_ms), peak, "multi_turn", tuned) if coarse_ms else None,
+        "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]},
+                     "shapes": [{"block": b, "chunk": c} for b, c in SCAN_SHAPES], "coarse_round_ms": tune_ms},
+        "e2e": {"value": seeds_per_step / (e2e / 1e3), "unit": "seeds/s", "ms_per_step": e2e,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "launches_per_step": launches_per_step,
+        "l2": "256 MiB flush before every step, issued on the step's stream inside the timed events "
+              "(~40 us per step counted against the result)",
+        "_cpu": (evs[0], q0["grid"]),
+    }
+
+
+def single_turn_leg(args, ws, rank, local, g, flush):
+    """The uniform-field single-turn configuration: 4000 seeds around the
+    truth of one event (40 uniform noise wires), ten rounds and the
+    classification; one event per call (latency) and 64 distinct events in
+    one call (throughput)."""
+    import torch
+    import cdc_synth as S
+    import paper_1908_01949_gb300 as cdc
+    cases = [S.cfg1_case(20_000 + 100 * rank + i) for i in range(64)]
+    fu = cases[0][1]
+    evs = [c[2] for c in cases]
+    grids = np.concatenate([c[3] for c in cases])
+    n1 = int(np.prod(grids[0]["n"]))
+    off, wid, dr = S.pack_events(evs)
+    tr = cdc.Tracker(g, fu, device=local, max_events=64, max_seeds=64 * n1, max_hits=int(wid.size))
+    sp = cdc.scan_params(h=H, max_steps=1000, lam=LAM, max_partitions=1, k=K, n_rounds=N_ROUNDS, n_zoom=N_ZOOM,
+                         max_drift=MAX_DRIFT)
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    gr_t = cdc.grids_to_tensor(grids, tr.dev)
+    one = tr.events_to_device([0, evs[0].wire_id.size], evs[0].wire_id, evs[0].drift)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    lat = timed(lambda: tr.scan(*one, gr_t[:1], sp), 5)
+    thr = timed(lambda: tr.scan(off_t, wid_t, dr_t, gr_t, sp), 3)
+    per_event = n1 + (N_ROUNDS - 1) * N_ZOOM * 243
+    return {"workload": "single-turn 104.97 MeV e-, uniform 1 T, 40 uniform noise wires; 8x4x5x5x5 = 4000-seed grid "
+                        "around the truth; 10 rounds; classification", "seeds_per_event": per_event,
+            "latency_ms_per_event": lat, "events_per_call": 64, "ms_per_call": thr,
+            "seeds_per_s": 64 * per_event / (thr / 1e3), "events_per_s": 64 / (thr / 1e3),
+            "timing": "median CUDA-event time, L2 flushed before each call"}
 
 
 def _gen_bidir(i):
@@ -609,48 +964,51 @@ def grid_value(gr, i):
                      for a in range(5)])
 
 
-REFINE_K, REFINE_SLOTS, REFINE_ITER, REFINE_CKPT, REFINE_SIGMA = 64, 1024, 5, 128, 0.2
+
+REFINE_K, REFINE_EVENTS, REFINE_ITER, REFINE_CKPT, REFINE_SIGMA = 64, 1024, 5, 128, 0.2
+REFINE_SCAN_SEEDS = 20_000
+
+
+def _gen_cfg4(i):
+    import cdc_synth as S
+    return S.cfg4_event(i, _GEN_FIELD, REFINE_SCAN_SEEDS)
 
 
 def refine_leg(args, rank, local, g, fm, stream):
-    """Throughput of cdc_refine_seeds on 1024 events x 64 seeds.  The seeds
-    are the 64 best of a ten-round scan of each distinct event; the event
-    slots repeat the distinct events (same hits), so every slot refines the
-    seeds its own scan selected."""
+    """Throughput of cdc_refine_seeds on the differentiable-refine
+    configuration: 1024 distinct events with 3-turn signals (10 % DIO-like
+    occupancy), 64 seeds each (65536 seeds): the 64 best of one batched
+    ten-round scan (k = 64) of a 2*10^4-seed grid around each event's first
+    turn; five Gauss-Newton iterations, checkpointed adjoint gradient, FP64
+    5x5 solves."""
     import torch
-    import cdc_synth as S
     import paper_1908_01949_gb300 as cdc
-    n_dist = max(1, int(args.refine_events))
-    evs = [S.cfg2_case(10_000 + 1000 * rank + i, fm, occupancy=0.10)[2] for i in range(n_dist)]
-    tmpl = S.cfg2_grid_template()
-    tr = cdc.Tracker(g, fm, device=local, max_events=REFINE_SLOTS, max_seeds=int(np.prod(tmpl["n"][0])),
-                     max_hits=1 << 20)
+    n_ev = max(1, int(args.refine_events))
+    evs, grids, S = make_batched_workload(n_ev, first=1000 * rank, gen=_gen_cfg4)
+    off, wid, dr = S.pack_events(evs)
+    n_scan = int(sum(int(np.prod(gr["n"])) for gr in grids))
+    tr = cdc.Tracker(g, fm, device=local, max_events=n_ev, max_seeds=n_scan, max_hits=int(wid.size))
     dev = tr.dev
-    hp = cdc.hough_params(grid_template=tmpl)
     sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=REFINE_K,
                          n_rounds=N_ROUNDS, n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
-    best = []
-    for ev in evs:
-        off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
-        h = tr.hough(off, wid, hp, stream=stream)
-        out = tr.scan(off, wid, dr, h["grid"], sp, want_hits=False, stream=stream)
-        best.append(out["best_seed"][0])
-    slot_ev = [evs[i % n_dist] for i in range(REFINE_SLOTS)]
-    hit_off = np.concatenate([[0], np.cumsum([e.wire_id.size for e in slot_ev])]).astype(np.int32)
-    off, wid, dr = tr.events_to_device(hit_off, np.concatenate([e.wire_id for e in slot_ev]),
-                                       np.concatenate([e.drift for e in slot_ev]))
-    seeds = torch.cat([best[i % n_dist] for i in range(REFINE_SLOTS)]).contiguous()
-    seed_event = torch.arange(REFINE_SLOTS, dtype=torch.int32, device=dev).repeat_interleave(REFINE_K)
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    t0 = time.perf_counter()
+    sc = tr.scan(off_t, wid_t, dr_t, cdc.grids_to_tensor(grids, dev), sp, want_hits=False, stream=stream)
+    torch.cuda.synchronize()
+    scan_s = time.perf_counter() - t0
+    seeds = sc["best_seed"].reshape(-1, 5).contiguous()
+    ok_seed = torch.isfinite(seeds).all(dim=1)
+    seed_event = torch.arange(n_ev, dtype=torch.int32, device=dev).repeat_interleave(REFINE_K)
     rp = cdc.refine_params(n_iter=REFINE_ITER, sigma=REFINE_SIGMA, checkpoint=REFINE_CKPT)
-    chi0 = tr.chi2_grad(seed_event, seeds, off, wid, dr, sp, rp, want_grad=False, stream=stream)["chi2"]
+    chi0 = tr.chi2_grad(seed_event, seeds, off_t, wid_t, dr_t, sp, rp, want_grad=False, stream=stream)["chi2"]
     for _ in range(max(1, min(args.warmup, 2))):
-        out = tr.refine(seed_event, seeds, off, wid, dr, sp, rp, stream=stream)
+        out = tr.refine(seed_event, seeds, off_t, wid_t, dr_t, sp, rp, stream=stream)
     torch.cuda.synchronize()
     times = []
     for _ in range(args.refine_reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        out = tr.refine(seed_event, seeds, off, wid, dr, sp, rp, stream=stream)
+        out = tr.refine(seed_event, seeds, off_t, wid_t, dr_t, sp, rp, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -660,11 +1018,15 @@ def refine_leg(args, rank, local, g, fm, stream):
     fl = out["flags"].cpu().numpy()
     ok = np.isfinite(c0) & np.isfinite(c1) & (c0 > 0)
     n = int(seeds.shape[0])
-    return {"seeds": n, "events": REFINE_SLOTS, "distinct_events": n_dist, "iterations": REFINE_ITER,
-            "checkpoint": REFINE_CKPT, "ms": ms, "seeds_per_s": n / (ms / 1e3),
-            "events_per_s": REFINE_SLOTS / (ms / 1e3),
+    return {"seeds": n, "events": n_ev, "distinct_events": n_ev, "seeds_per_event": REFINE_K,
+            "turns": 3, "iterations": REFINE_ITER, "checkpoint": REFINE_CKPT, "ms": ms,
+            "seeds_per_s": n / (ms / 1e3), "events_per_s": n_ev / (ms / 1e3),
+            "finite_start_seeds": int(ok_seed.sum().item()),
             "median_chi2_ratio": float(np.median(c1[ok] / c0[ok])) if ok.any() else None,
-            "flagged": int((fl != 0).sum()), "timing": f"median of {args.refine_reps} CUDA-event timed calls"}
+            "flagged": int((fl != 0).sum()),
+            "seed_selection": f"64 best of one batched ten-round scan (k = 64) of {REFINE_SCAN_SEEDS} seeds per "
+                              f"event around its first turn ({scan_s:.2f} s, not timed)",
+            "timing": f"median of {args.refine_reps} CUDA-event timed calls"}
 
 
 # --------------------------------------------------------------- CUDA arm
@@ -681,287 +1043,151 @@ def run_cuda(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    g, fm, ev = make_workload(rank)
-    tmpl = S.cfg2_grid_template()
-    if args.profile_case:
-        tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
-    seeds_coarse = int(np.prod(tmpl["n"][0]))
-    seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
-    hp = cdc.hough_params(grid_template=tmpl)
-    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
-                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
-    off_h = torch.tensor([0, ev.wire_id.size], dtype=torch.int32).pin_memory()
-    wid_h = torch.from_numpy(ev.wire_id.astype(np.int32)).pin_memory()
-    dr_h = torch.from_numpy(ev.drift.astype(np.float32)).pin_memory()
-    nh = int(wid_h.numel())
-    ne = 1
-    n_in = max(1, int(args.inflight))
-
-    def make_slot(k):
-        """One event in flight: its own context (workspace), stream and buffers."""
-        t = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=seeds_coarse, max_hits=4096)
-        d = dict(tr=t, ctx=t.ctx, stream=torch.cuda.current_stream() if k == 0 else torch.cuda.Stream(device=dev),
-                 off=off_h.to(dev), wid=wid_h.to(dev), dr=dr_h.to(dev),
-                 acc=torch.empty((ne, hp.n_bins, hp.n_bins), dtype=torch.int32, device=dev),
-                 cand=torch.empty((ne, hp.max_cand, 28), dtype=torch.uint8, device=dev),
-                 ncand=torch.empty(ne, dtype=torch.int32, device=dev),
-                 grid=torch.empty((ne, cdc.GRID_BYTES), dtype=torch.uint8, device=dev),
-                 hflags=torch.empty(ne, dtype=torch.int32, device=dev),
-                 best_E=torch.empty((ne, K), dtype=torch.float32, device=dev),
-                 best_seed=torch.empty((ne, K, 5), dtype=torch.float32, device=dev),
-                 topk0=torch.empty((ne, K), dtype=torch.int64, device=dev),
-                 hit_part=torch.empty(nh, dtype=torch.int8, device=dev),
-                 sflags=torch.empty(ne, dtype=torch.int32, device=dev),
-                 steps=torch.zeros(N_ROUNDS, dtype=torch.int64, device=dev),
-                 out_E=torch.empty((ne, K), dtype=torch.float32).pin_memory(),
-                 out_S=torch.empty((ne, K, 5), dtype=torch.float32).pin_memory(),
-                 out_P=torch.empty(nh, dtype=torch.int8).pin_memory(),
-                 out_F=torch.empty(ne, dtype=torch.int32).pin_memory())
-        return d
-
-    slots = [make_slot(k) for k in range(n_in)]
-    tr, ctx, stream = slots[0]["tr"], slots[0]["ctx"], slots[0]["stream"]
-    off, wid, dr, grid = slots[0]["off"], slots[0]["wid"], slots[0]["dr"], slots[0]["grid"]
-
-    def step(q, h2d=False, d2h=False):
-        """One event through the hot path on slot q's stream; with h2d / d2h the
-        inputs come from pinned host memory and the results go back to it."""
-        st = q["stream"]
-        with torch.cuda.stream(st):
-            if h2d:
-                q["off"].copy_(off_h, non_blocking=True)
-                q["wid"].copy_(wid_h, non_blocking=True)
-                q["dr"].copy_(dr_h, non_blocking=True)
-            q["ctx"].cdc_hough_seeds(ne, q["off"], q["wid"], hp, q["acc"], q["cand"], q["ncand"], q["grid"],
-                                     q["hflags"], st)
-            q["ctx"].cdc_scan_seeds(ne, q["off"], q["wid"], q["dr"], q["grid"], sp, None, q["topk0"], q["best_E"],
-                                    q["best_seed"], q["hit_part"], None, None, q["sflags"], q["steps"], st)
-            if d2h:
-                q["out_E"].copy_(q["best_E"], non_blocking=True)
-                q["out_S"].copy_(q["best_seed"], non_blocking=True)
-                q["out_P"].copy_(q["hit_part"], non_blocking=True)
-                q["out_F"].copy_(q["sflags"], non_blocking=True)
-
-    grid_for_tuning(ctx, ne, off, wid, hp, slots[0]["acc"], slots[0]["cand"], slots[0]["ncand"], grid,
-                    slots[0]["hflags"], stream)
-    if args.scan_shape:
-        tuned = tuple(int(x) for x in args.scan_shape.split(","))
-        tune_ms = None
-    else:
-        tuned, tune_ms = tr.tune(off, wid, dr, grid, sp, reps=3, stream=stream)
-    # zoom rounds (972 seeds per event): one event at a time, one warp per seed
-    # shortens them (latency); with many events in flight one lane per seed
-    # leaves the other events' coarse rounds the warp slots (throughput)
-    lat_ws = args.warp_seeds if args.warp_seeds is not None else ctx.cdc_get_scan_config()[2]
-    thr_ws = args.stream_warp_seeds
-    for q in slots:
-        q["ctx"].cdc_set_scan_config(*tuned, thr_ws)
-    ctx.cdc_set_scan_config(*tuned, lat_ws)
-    # Hough vote + peaks; table clear + staging; block order of the coarse grid; per round prologue, scan,
-    # top-K partial + merge, best merge; a zoom grid build per zoom round; hit assignment
-    launches_per_step = 2 + 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
+    g = S.make_geometry()
+    fm = S.solenoid_map()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    for i in range(args.warmup * n_in):
-        step(slots[i % n_in])
-    torch.cuda.synchronize()
-
-    # latency and the roofline: one event at a time on one stream, the library's
-    # CUDA events around every scan-kernel launch
-    q0 = slots[0]
-    q0["steps"].zero_()
-    ctx.cdc_kernel_timer(True)
-    lat_ms = []
-    for i in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(q0)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        lat_ms.append(e0.elapsed_time(e1))
-    _, _, kper = ctx.cdc_kernel_time()
-    ctx.cdc_kernel_timer(False)
-    ctx.cdc_set_scan_config(*tuned, thr_ws)
-    rkn = q0["steps"].cpu().numpy().astype(np.float64)
-    coarse_ms = [float(kper[i]) for i in range(0, len(kper), N_ROUNDS)]
-    coarse_steps = float(rkn[0]) / args.steps
-    latency = statistics.median(lat_ms)
-
-    # throughput: a stream of events, n_in of them in flight (one context and
-    # stream each, round robin); every step is one event's whole hot path
-    def run_stream(h2d=False, d2h=False):
-        main = torch.cuda.current_stream()
-        for q in slots:
-            q["steps"].zero_()
-            q["stream"].wait_stream(main)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
-        e0.record(main)
-        for i in range(args.steps):
-            q = slots[i % n_in]
-            with torch.cuda.stream(q["stream"]):
-                flush.zero_()
-            step(q, h2d, d2h)
-        for q in slots:
-            main.wait_stream(q["stream"])
-        e1.record(main)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3
-
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
-    (dev_ms, wall), clocks = timed_region(run_stream, sampler, torch.cuda.synchronize, dist, dev)
-    ms = reduce_max(dev_ms / args.steps, dist, dev)
-    rkn_per_step = float(sum(q["steps"].sum().item() for q in slots)) / args.steps
-    # roofline of the dominant kernel (coarse-round scan launch), ALU bound
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    f_step = flops_per_step(1)
-    achieved = f_step * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12 if coarse_ms else None
-    executed = (FP32_COUNTS["fp32_ops_per_rkn_step"] * coarse_steps / (statistics.mean(coarse_ms) / 1e3) / 1e12
-                if coarse_ms else None)
+    probe = cdc.Tracker(g, fm, device=local, max_events=1, max_seeds=1, max_hits=1)
+    peak = fp32_peak(probe, sampler)
+    stream = torch.cuda.current_stream()
 
-    # end to end: the same stream of events with each step's inputs copied from
-    # pinned host memory and its results (best seeds and scores, hit classes,
-    # flags) copied back inside the timed region; host wall clock
-    _, e2e_wall = run_stream(h2d=True, d2h=True)
-    e2e = e2e_wall / args.steps
-    h2d = int(off_h.numel() * 4 + wid_h.numel() * 4 + dr_h.numel() * 4)
-    d2h = int(q0["out_E"].numel() * 4 + q0["out_S"].numel() * 4 + q0["out_P"].numel() + q0["out_F"].numel() * 4)
-    wall = wall / 1e3
+    if args.profile_case:
+        mt = multi_turn_leg(args, ws, rank, local, g, fm, flush, peak)
+        if rank == 0:
+            mt.pop("_cpu")
+            print(json.dumps({"metric": METRIC, "value": mt["seeds_per_s"], "unit": "seeds/s", "n_gpus": ws,
+                              "steps": args.mt_steps, "warmup": args.warmup, "ms_per_step": mt["ms_per_step"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic",
+                              "config": {"workload": WORKLOAD_MULTI_TURN, "profile_case":
+                                         "240000-seed coarse grid for profiler captures, not a benchmark result"},
+                              "coarse_scan": {"launch_ms": mt["roofline"]["launch_ms"],
+                                              "rkn_steps": mt["roofline"]["rkn_steps"]},
+                              "latency_ms_per_event": mt["latency_ms_per_event"], "multi_turn": mt,
+                              "fp32_peak": peak}))
+        if dist:
+            dist.destroy_process_group()
+        return
 
-    refine = None
-    if not args.no_refine and not args.profile_case:
-        refine = guarded('refine', lambda: refine_leg(args, rank, local, g, fm, stream))
-    batched = None
-    if not args.no_batched and not args.profile_case:
-        batched = guarded('batched', lambda: batched_leg(args, rank, local, g, fm, flush))
-    sweep = None
-    if not args.no_sweep and not args.profile_case:
-        sweep = guarded('sweep', lambda: sweep_leg(args, rank, local, g, fm, flush))
-    loop = None
-    if not args.no_loop and not args.profile_case:
-        loop = guarded('loop', lambda: event_loop_leg(args, rank, local, g, fm))
-    split_ab = None
-    if not args.no_split and not args.profile_case:
-        split_ab = guarded('split_ab', lambda: split_ab_leg(args, rank, local, g, fm, ev, grid, flush))
-    bidir = None
-    if not args.no_bidir and not args.profile_case:
-        bidir = guarded('bidir', lambda: bidirectional_leg(args, rank, local, g, fm, flush))
+    head = headline_batched(args, ws, rank, local, dist, g, fm, flush, sampler, peak)
+    work = head.pop("workload")
+    legs = {}
+    if not args.no_multi_turn:
+        legs["multi_turn"] = guarded("multi_turn", lambda: multi_turn_leg(args, ws, rank, local, g, fm, flush, peak))
+    if not args.no_single_turn:
+        legs["single_turn"] = guarded("single_turn", lambda: single_turn_leg(args, ws, rank, local, g, flush))
+    if not args.no_refine:
+        legs["refine"] = guarded("refine", lambda: refine_leg(args, rank, local, g, fm, stream))
+    if not args.no_sweep:
+        legs["sweep"] = guarded("sweep", lambda: sweep_leg(args, rank, local, g, fm, flush))
+    if not args.no_loop:
+        legs["event_loop"] = guarded("loop", lambda: event_loop_leg(args, rank, local, g, fm))
+    mt_cpu = legs.get("multi_turn", {}).pop("_cpu", None) if isinstance(legs.get("multi_turn"), dict) else None
+    if not args.no_split and mt_cpu is not None:
+        legs["split_ab"] = guarded("split_ab", lambda: split_ab_leg(args, rank, local, g, fm, mt_cpu[0], mt_cpu[1],
+                                                                     flush))
+    if not args.no_bidir:
+        legs["bidirectional"] = guarded("bidir", lambda: bidirectional_leg(args, rank, local, g, fm, flush))
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ev, g, fm, grid, target_s=args.cpu_seconds)
-        if refine is not None:
-            cpu["refine"] = guarded('cpu_refine', lambda: cpu_refine_baseline(g, fm, args.refine_events))
+        cpu = guarded("cpu_baseline", lambda: cpu_baseline(work, g, fm, target_s=args.cpu_seconds))
+        if isinstance(legs.get("refine"), dict) and "seeds_per_s" in legs["refine"]:
+            cpu["refine"] = guarded("cpu_refine", lambda: cpu_refine_baseline(g, fm, 16))
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    refine = legs.get("refine") or {}
     line = {
-        "metric": METRIC, "value": job_value(ws, seeds_per_step, ms), "unit": "seeds/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "metric": METRIC, "value": job_value(ws, head["seeds_step"], head["ms"]), "unit": "seeds/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "seeds_per_step": seeds_per_step, "events_per_step": 1,
-                   "events_in_flight": n_in,
-                   "zoom_rounds": {"throughput_run": "warp per seed" if thr_ws >= N_ZOOM * 243 else "lane per seed",
-                                   "latency_run": "warp per seed" if lat_ws >= N_ZOOM * 243 else "lane per seed"},
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"event-parallel x{ws} (independent events per GPU, no collective)"},
-        "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
-        "latency_ms_per_event": latency,
-        "coarse_scan": {"launch_ms": statistics.mean(coarse_ms) if coarse_ms else None, "rkn_steps": coarse_steps,
-                        "seeds": seeds_coarse},
-        "autotune": {"config": {"block": tuned[0], "chunk": tuned[1]},
-                     "shapes": [{"block": b, "chunk": c} for b, c in SCAN_SHAPES], "coarse_round_ms": tune_ms},
-        "refine_seeds_per_s": refine.get("seeds_per_s") if refine else None,
-        "refine": refine,
-        "batched": batched,
-        "sweep": sweep,
-        "bidirectional": bidir,
-        "split_ab": split_ab,
-        "event_loop": loop,
-        "events_per_s": {"scan": ws / (ms / 1e3),
-                         "refine": ws * refine["events_per_s"] if refine and "events_per_s" in refine else None},
-        "roofline": {"bound": "alu", "kernel": "scan_kernel<map> (coarse round)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": TRAFFIC["bytes"] if csrc_digest() == TRAFFIC["csrc_sha256"] else None,
-                     "traffic_note": "DRAM bytes per coarse launch, one ncu capture (see profiles/) at launch shape "
-                                     f"{TRAFFIC['shape']} (block x chunk); this run's shape "
-                                     f"{tuned[0]}x{tuned[1]}: the shapes run the same per-seed code and "
-                                     "differ in threads per block and steps between seed refills",
-                     "ncu_fp32": ({"fp32_ops_per_rkn_step": FP32_COUNTS["fp32_ops_per_rkn_step"],
-                                   "fma_pipe_active_pct_240k_case": FP32_COUNTS["fma_pipe_active_pct"],
-                                   "executed_tflops": executed,
-                                   "executed_fp32_frac_of_peak": executed / peak if executed else None,
-                                   "note": "all executed FP32 work (FFMA = 2) per RKN step from ncu, times this "
-                                           "launch's steps over its CUDA-event time"}
-                                  if csrc_digest() == FP32_COUNTS["csrc_sha256"] else None),
-                     "flops_per_rkn_step": f_step,
-                     "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                   f"{sm_max:.0f} MHz (unit counts and max clock)"},
-        "e2e": {"value": seeds_per_step / (e2e / 1e3), "unit": "seeds/s", "ms_per_step": e2e,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks,
-        "wall_s": wall,
+        "config": {"workload": WORKLOAD, "events_per_step": head["n_events"], "seeds_per_step": head["seeds_step"],
+                   "l2": "256 MiB flush before every replay, outside its timed events",
+                   "parallelism": f"event-parallel x{ws} (each GPU its own 256 events, no collective)"},
+        "rkn_steps_per_s": job_value(ws, head["rkn_step"], head["ms"]),
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches_per_step"] * args.steps,
+        "clocks": head["clocks"],
+        "fp32_peak": peak,
+        "batched": head["detail"],
+        "refine_seeds_per_s": refine.get("seeds_per_s"),
+        **legs,
         "cpu_baseline": cpu,
     }
-    if args.profile_case:
-        line["config"]["profile_case"] = "240000-seed coarse grid for profiler captures, not a benchmark result"
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-def cpu_baseline(ev, g, fm, grid_t, target_s=15.0):
-    """FP64 oracle on a bounded random sample of this step's coarse seeds,
-    all host cores (threads split the seeds)."""
+def sample_workload_seeds(work, n, rng):
+    """n seeds drawn uniformly from all coarse seeds of the batched workload:
+    (event index, seed values) pairs."""
+    counts = np.asarray(work["counts"], np.int64)
+    base = np.concatenate([[0], np.cumsum(counts)])
+    pick = np.sort(rng.choice(int(base[-1]), size=min(n, int(base[-1])), replace=False))
+    ev_of = np.searchsorted(base, pick, side="right") - 1
+    return [(int(e), grid_value(work["grids"][e], int(i - base[e]))) for e, i in zip(ev_of, pick)]
+
+
+def oracle_on_sample(work, g, fm, sample, threads):
+    """FP64 oracle scores of sampled seeds of the batched workload, events in
+    parallel on `threads` host threads (one oracle call per event)."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle as O
-    import paper_1908_01949_gb300 as cdc
-    grid = cdc.tensor_to_grids(grid_t)
-    seeds = O.grid_values(grid[0:1])
-    rng = np.random.default_rng(0)
     P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
+    by_ev = {}
+    for e, sd in sample:
+        by_ev.setdefault(e, []).append(sd)
+
+    def one(item):
+        e, sds = item
+        ev = work["evs"][e]
+        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), np.asarray(sds, np.float64), P, threads=1)
+        return int(r["n_steps"].sum())
+
+    with ThreadPoolExecutor(threads) as ex:
+        return sum(ex.map(one, sorted(by_ev.items())))
+
+
+def cpu_baseline(work, g, fm, target_s=15.0):
+    """FP64 oracle on a bounded random sample of the headline's coarse seeds,
+    all host cores (events in parallel), and one core."""
     cores = os.cpu_count() or 1
-    n = cores
-    t = 0.0
-    done = 0
-    steps = 0
-    while t < target_s and done < seeds.shape[0]:
-        idx = rng.choice(seeds.shape[0], size=min(n, seeds.shape[0]), replace=False)
+    rng = np.random.default_rng(0)
+    n, t, done, steps = 2 * cores, 0.0, 0, 0
+    while t < target_s:
+        sample = sample_workload_seeds(work, n, rng)
         t0 = time.perf_counter()
-        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=cores)
+        steps += oracle_on_sample(work, g, fm, sample, cores)
         t += time.perf_counter() - t0
-        done += idx.size
-        steps += int(r["n_steps"].sum())
+        done += len(sample)
         n *= 2
-    # one core, as the paper's serialised CPU comparison (sec. 3.1), on a smaller sample
     t1, done1, steps1, n1 = 0.0, 0, 0, 8
-    while t1 < min(5.0, target_s / 3) and done1 < seeds.shape[0]:
-        idx = rng.choice(seeds.shape[0], size=min(n1, seeds.shape[0]), replace=False)
+    while t1 < min(5.0, target_s / 3):
+        sample = sample_workload_seeds(work, n1, rng)
         t0 = time.perf_counter()
-        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=1)
+        steps1 += oracle_on_sample(work, g, fm, sample, 1)
         t1 += time.perf_counter() - t0
-        done1 += idx.size
-        steps1 += int(r["n_steps"].sum())
+        done1 += len(sample)
         n1 *= 2
-    return {"value": done / t, "unit": "seeds/s", "cores": cores, "kind": "oracle",
-            "rkn_steps_per_s": steps / t,
+    return {"value": done / t, "unit": "seeds/s", "cores": cores, "kind": "oracle", "rkn_steps_per_s": steps / t,
             "one_core": {"value": done1 / t1, "unit": "seeds/s", "rkn_steps_per_s": steps1 / t1,
                          "sample": f"{done1} seeds, {t1:.1f} s, one thread"},
-            "sample": f"{done} seeds drawn at random from the step's 10^6-seed coarse grid, same event and "
-                      f"parameters, {t:.1f} s"}
+            "sample": f"{done} seeds drawn at random from all coarse seeds of the step's "
+                      f"{len(work['evs'])} events, same events and parameters, {t:.1f} s"}
 
 
 def cpu_refine_baseline(g, fm, n_dist, target_s=3.0):
     """FP64 oracle refinement, one thread, on a bounded sample: seeds near
-    the first-turn truth of the refine leg's distinct events (seeded noise),
+    the first-turn truth of the refine leg's first events (seeded noise),
     each classified at its start and refined with the leg's iterations."""
     import cdc_synth as S
     import oracle as O
     P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
-    evs = [S.cfg2_case(10_000 + i, fm, occupancy=0.10)[2] for i in range(max(1, n_dist))]
+    evs = [S.cfg4_event(i, fm, REFINE_SCAN_SEEDS)[0] for i in range(max(1, n_dist))]
     rng = np.random.default_rng(4)
     sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * 0.3
     t, done = 0.0, 0
@@ -982,42 +1208,42 @@ def cpu_refine_baseline(g, fm, n_dist, target_s=3.0):
 
 # --------------------------------------------------------- reference arm
 def run_reference(args, ws, rank, local):
+    """The FP64 oracle, as it stands, timed on the host cores on the headline's
+    configuration: each step scores a bounded random sample of the batched
+    workload's coarse seeds (events in parallel on all cores)."""
     if rank != 0:
         return
-    import cdc_synth as S
     import oracle as O
+    import cdc_synth as S
     oracle_build = O.build()
-    g, fm, ev = make_workload(0)
-    H_ = O.hough_params()
-    _, _, cen = O.hough(g, H_, ev.wire_id)
-    tmpl = S.cfg2_grid_template()
-    if cen.shape[0]:
-        tmpl["centre"][0][[0, 2, 3]] = cen[0]
-    seeds = O.grid_values(tmpl)
-    P = O.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART)
+    g, fm = S.make_geometry(), S.solenoid_map()
+    evs, grids, _ = make_batched_workload(int(args.batched_events))
+    work = {"evs": evs, "grids": grids, "counts": [int(np.prod(gr["n"])) for gr in grids]}
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(1)
     per_step = max(cores, int(args.ref_seeds))
     times, done, nsteps = [], 0, 0
     for i in range(args.warmup + args.steps):
-        idx = rng.choice(seeds.shape[0], size=per_step, replace=False)
+        sample = sample_workload_seeds(work, per_step, rng)
         t0 = time.perf_counter()
-        r = O.scan(g, fm, ev.wire_id, ev.drift.astype(np.float64), seeds[idx], P, threads=cores)
+        st = oracle_on_sample(work, g, fm, sample, cores)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
-            done += per_step
-            nsteps += int(r["n_steps"].sum())
+            done += len(sample)
+            nsteps += st
     tot = sum(times)
     v = done / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "seeds/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "seeds_per_step": per_step,
-                       "sample": f"{per_step} seeds per step drawn from the 10^6-seed grid of the same event"},
+                       "sample": f"{per_step} seeds per step drawn at random from all coarse seeds of the "
+                                 f"{len(evs)} events"},
             "rkn_steps_per_s": nsteps / tot,
             "cpu_baseline": {"value": v, "unit": "seeds/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} random seeds of the coarse grid per step ({oracle_build})"},
+                             "sample": f"{per_step} random coarse seeds of the batched workload per step "
+                                       f"({os.path.relpath(oracle_build, ROOT)})"},
             "e2e": {"value": v, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -1025,18 +1251,21 @@ def run_reference(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10, help="timed graph replays of the batched step")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="end-to-end steps (at most --steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seeds", type=int, default=512, help="oracle seeds per step of the reference arm")
+    ap.add_argument("--batched-events", type=int, default=256, help="events of the batched step")
+    ap.add_argument("--no-multi-turn", action="store_true", help="skip the single-event multi-turn leg")
+    ap.add_argument("--mt-steps", type=int, default=40, help="events per run of the multi-turn leg")
+    ap.add_argument("--no-single-turn", action="store_true", help="skip the single-turn leg")
     ap.add_argument("--no-refine", action="store_true", help="skip the refine leg")
-    ap.add_argument("--refine-events", type=int, default=16, help="distinct events of the refine leg")
+    ap.add_argument("--refine-events", type=int, default=REFINE_EVENTS, help="distinct events of the refine leg")
     ap.add_argument("--refine-reps", type=int, default=3, help="timed refine calls (median)")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched 256-event leg")
-    ap.add_argument("--batched-events", type=int, default=256, help="events of the batched leg")
-    ap.add_argument("--batched-steps", type=int, default=3, help="timed graph replays of the batched leg")
+    ap.add_argument("--batched-steps", type=int, default=3, help="timed graph replays of the sweep leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 30 %%-occupancy precision/scale leg")
     ap.add_argument("--sweep-events", type=int, default=64, help="events of the sweep leg")
     ap.add_argument("--no-bidir", action="store_true", help="skip the bidirectional-scan leg")
@@ -1048,14 +1277,14 @@ def main():
     ap.add_argument("--scan-shape", default=None,
                     help="fixed scan-kernel shape 'block,chunk' instead of autotuning (profiler captures)")
     ap.add_argument("--warp-seeds", type=int, default=None,
-                    help="latency run: zoom rounds with at most this many seeds run one warp per seed (0: never; "
-                         "default: the library's, 16 per SM)")
+                    help="multi-turn latency run: zoom rounds with at most this many seeds run one warp per seed "
+                         "(0: never; default: the library's, 16 per SM)")
     ap.add_argument("--stream-warp-seeds", type=int, default=0,
-                    help="the same for the throughput and end-to-end runs (default 0: one lane per seed)")
+                    help="the same for the multi-turn throughput and end-to-end runs (default 0: one lane per seed)")
     ap.add_argument("--inflight", type=int, default=8,
-                    help="events in flight (one context and stream each) in the throughput run")
+                    help="distinct events in flight (one context and stream each) in the multi-turn leg")
     ap.add_argument("--profile-case", action="store_true",
-                    help="reduced 240000-seed coarse grid for profiler captures (not a benchmark result)")
+                    help="only the multi-turn leg on a 240000-seed coarse grid (profiler captures; not a result)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

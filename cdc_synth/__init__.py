@@ -6,15 +6,20 @@ shaped like the workloads of the paper (sec. 1: 18 stereo sense layers, 1 T
 solenoid, 104.97 MeV signal electrons from an aluminium target; sec. 2.1:
 seeds defined at R0 = 50 cm).  It holds none of the track finder's arithmetic:
 the truth tracks are made with the closed-form helix (uniform field) or a
-classical 6-D Runge-Kutta simulation (field map), and the hits with a plain
-dense-sampling distance search.  Both the FP64 oracle and the CUDA library
+classical 6-D Runge-Kutta simulation (field map; a small C loop in _sim.c,
+built with gcc on first use), and the hits with a plain dense-sampling
+distance search.  Both the FP64 oracle and the CUDA library
 consume what it returns; neither is imported here.
 
 Units: mm, MeV/c, T, rad.  Electron charge q = -1.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -180,34 +185,58 @@ def solenoid_map(nr: int = 451, nz: int = 1001, r_min: float = 0.0, z_min: float
                  br=(br * scale).astype(np.float32), r_min=r_min, z_min=z_min, dr=dr, dz=dz)
 
 
-def _field_sim(f: Field, x: float, y: float, z: float):
-    """Field used by the truth simulation: bilinear in (r, z) of the samples."""
-    if f.kind == 0:
-        return 0.0, 0.0, f.B0
-    rho = math.hypot(x, y)
-    u = (min(max(rho, f.r_min), f.r_min + f.dr * (f.nr - 1)) - f.r_min) / f.dr
-    v = (min(max(z, f.z_min), f.z_min + f.dz * (f.nz - 1)) - f.z_min) / f.dz
-    i = min(int(u), f.nr - 2)
-    j = min(int(v), f.nz - 2)
-    u -= i
-    v -= j
-    w00, w10, w01, w11 = (1 - u) * (1 - v), u * (1 - v), (1 - u) * v, u * v
-    bz = (w00 * float(f.bz[i, j]) + w10 * float(f.bz[i + 1, j]) +
-          w01 * float(f.bz[i, j + 1]) + w11 * float(f.bz[i + 1, j + 1]))
-    br = (w00 * float(f.br[i, j]) + w10 * float(f.br[i + 1, j]) +
-          w01 * float(f.br[i, j + 1]) + w11 * float(f.br[i + 1, j + 1]))
-    if rho < 1e-12:
-        return 0.0, 0.0, bz
-    return br * x / rho, br * y / rho, bz
-
-
 # -------------------------------------------------------- truth simulation
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SIM_SRC = os.path.join(_HERE, "_sim.c")
+_SIM_LIB = os.path.join(_HERE, "_build", "libsynth.so")
+_sim = None
+_sim_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the field-map truth simulator (_sim.c) with gcc, no FMA
+    contraction, so every machine produces the same events."""
+    os.makedirs(os.path.dirname(_SIM_LIB), exist_ok=True)
+    if force or not os.path.exists(_SIM_LIB) or os.path.getmtime(_SIM_LIB) < os.path.getmtime(_SIM_SRC):
+        tmp = _SIM_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                               _SIM_SRC, "-lm"])
+        os.replace(tmp, _SIM_LIB)
+    return _SIM_LIB
+
+
+def _sim_lib():
+    global _sim
+    with _sim_lock:
+        if _sim is None:
+            L = ctypes.CDLL(build())
+            d, i, pd, pf = ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+            L.synth_track_map.argtypes = [pf, pf, i, i, d, d, d, d, d, pd, pd, d, i, d, d, pd, pd]
+            L.synth_track_map.restype = i
+            _sim = L
+    return _sim
+
+
+def _map_track(f: "Field", r0, t0, lam, ds, n, z_stop, r_stop):
+    bz = np.ascontiguousarray(f.bz, dtype=np.float32)
+    br = np.ascontiguousarray(f.br, dtype=np.float32)
+    r0 = np.ascontiguousarray(r0, dtype=np.float64)
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    pos = np.empty((n, 3))
+    dirs = np.empty((n, 3))
+    pf, pd = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+    m = _sim_lib().synth_track_map(bz.ctypes.data_as(pf), br.ctypes.data_as(pf), f.nr, f.nz, f.r_min, f.z_min, f.dr,
+                                   f.dz, lam, r0.ctypes.data_as(pd), t0.ctypes.data_as(pd), ds, n, z_stop, r_stop,
+                                   pos.ctypes.data_as(pd), dirs.ctypes.data_as(pd))
+    return pos[:m], dirs[:m]
+
+
 def simulate_track(f: Field, r0, p0, q: float = -1.0, max_len: float = 8000.0,
                    ds: float = 1.0, z_stop: float = 800.0, r_stop: float = 900.0):
     """Truth trajectory sampled every ds mm: returns (pos [n,3], dir [n,3]).
 
-    Uniform field: closed-form helix.  Map: classical RK4 on (r, t) with step ds.
-    Stops once |z| > z_stop or rho > r_stop or after max_len."""
+    Uniform field: closed-form helix.  Map: classical RK4 on (r, t) with step ds
+    (_sim.c).  Stops once |z| > z_stop or rho > r_stop or after max_len."""
     r0 = np.asarray(r0, dtype=np.float64)
     p0 = np.asarray(p0, dtype=np.float64)
     p = float(np.linalg.norm(p0))
@@ -223,42 +252,7 @@ def simulate_track(f: Field, r0, p0, q: float = -1.0, max_len: float = 8000.0,
         dirs = np.stack([t0[0] * cw + t0[1] * sw, t0[1] * cw - t0[0] * sw,
                          np.full_like(s, t0[2])], 1)
     else:
-        lam = q * KAPPA / p
-        pos = np.empty((n, 3))
-        dirs = np.empty((n, 3))
-        x, y, z = r0
-        tx, ty, tz = t0
-
-        def acc(x, y, z, tx, ty, tz):
-            bx, by, bz = _field_sim(f, x, y, z)
-            return (lam * (ty * bz - tz * by), lam * (tz * bx - tx * bz), lam * (tx * by - ty * bx))
-
-        for i in range(n):
-            pos[i] = (x, y, z)
-            dirs[i] = (tx, ty, tz)
-            a1 = acc(x, y, z, tx, ty, tz)
-            h2 = 0.5 * ds
-            a2 = acc(x + h2 * tx, y + h2 * ty, z + h2 * tz,
-                     tx + h2 * a1[0], ty + h2 * a1[1], tz + h2 * a1[2])
-            b2 = (tx + h2 * a1[0], ty + h2 * a1[1], tz + h2 * a1[2])
-            a3 = acc(x + h2 * b2[0], y + h2 * b2[1], z + h2 * b2[2],
-                     tx + h2 * a2[0], ty + h2 * a2[1], tz + h2 * a2[2])
-            b3 = (tx + h2 * a2[0], ty + h2 * a2[1], tz + h2 * a2[2])
-            b4 = (tx + ds * a3[0], ty + ds * a3[1], tz + ds * a3[2])
-            a4 = acc(x + ds * b3[0], y + ds * b3[1], z + ds * b3[2], b4[0], b4[1], b4[2])
-            x += ds / 6 * (tx + 2 * b2[0] + 2 * b3[0] + b4[0])
-            y += ds / 6 * (ty + 2 * b2[1] + 2 * b3[1] + b4[1])
-            z += ds / 6 * (tz + 2 * b2[2] + 2 * b3[2] + b4[2])
-            tx += ds / 6 * (a1[0] + 2 * a2[0] + 2 * a3[0] + a4[0])
-            ty += ds / 6 * (a1[1] + 2 * a2[1] + 2 * a3[1] + a4[1])
-            tz += ds / 6 * (a1[2] + 2 * a2[2] + 2 * a3[2] + a4[2])
-            if abs(z) > z_stop or math.hypot(x, y) > r_stop:
-                if i + 1 < n:
-                    pos[i + 1] = (x, y, z)
-                    dirs[i + 1] = (tx, ty, tz)
-                    n = i + 2
-                break
-        pos, dirs = pos[:n], dirs[:n]
+        pos, dirs = _map_track(f, r0, t0, q * KAPPA / p, ds, n, z_stop, r_stop)
     rho = np.hypot(pos[:, 0], pos[:, 1])
     out = np.nonzero((np.abs(pos[:, 2]) > z_stop) | (rho > r_stop))[0]
     if out.size:
@@ -572,6 +566,20 @@ def cfg3_case(n_events: int = CFG3_EVENTS, field_map: Field | None = None, seeds
     out = [cfg3_event(first + i, f, seeds) for i in range(n_events)]
     grids = np.concatenate([gr for _, gr in out])
     return make_geometry(), f, [ev for ev, _ in out], grids
+
+
+CFG4_EVENTS = 1024
+
+
+def cfg4_event(index: int, field_map: Field | None = None, n_seeds: float = 2.0e4):
+    """One event of the differentiable-refine workload: a 3-turn e- with DIO-like
+    noise at 10 % occupancy, and a scaled multi-turn grid of ~n_seeds seeds
+    around its first turn from which a scan selects the seeds to refine."""
+    rng = np.random.default_rng(BASE_SEED + 4000 + index)
+    g = make_geometry()
+    f = field_map if field_map is not None else solenoid_map()
+    ev = make_event(g, f, rng, turns=(3,), noise="dio", occupancy=0.10)
+    return ev, scaled_grid(ev.truth_seeds[0], n_seeds, rng)
 
 
 CFG5_EVENTS = 64

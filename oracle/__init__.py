@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg and reference arm are the only users.  The arithmetic lives in oracle.c
 (plain C, double precision); this module builds it with gcc, marshals numpy
 arrays through ctypes, and adds the steps that are library primitives (sort
-for the top-K) or plain control flow (the ten-round zoom of sec. 2.2).
+for the top-K) or plain control flow over the C routines: the repeated scan
+around the best seeds (zoom_scan, sec. 2.2) and the event loop over turn
+partitions (event_loop, sec. 2.3, Fig. 7).
 It imports nothing from the CUDA package.
 """
 from __future__ import annotations
@@ -351,3 +353,123 @@ def extrapolate_turn(g, f, seed, params: ScanParams, direction):
     st = L.orc_extrapolate_turn(C.byref(G), C.byref(F), C.byref(params), _p(s, C.c_double), int(direction),
                                 _p(out, C.c_double))
     return out, int(st)
+
+
+# ----------------------------------------------------------- repeated scan
+_GRID = np.dtype([("centre", np.float32, 5), ("step", np.float32, 5), ("n", np.int32, 5)])
+
+
+def _grid(centre, step, n):
+    g = np.zeros(1, dtype=_GRID)
+    g["centre"][0] = centre
+    g["step"][0] = step
+    g["n"][0] = n
+    return g
+
+
+def zoom_scan(g, f, wire_id, drift, grid, params: ScanParams, k=8, n_rounds=10, n_zoom=4, threads=None):
+    """Sec. 2.2: the scan repeated around its best seeds ("repeated ten times").
+    Round 0 scores every seed of `grid`.  Round r = 1 .. n_rounds-1 takes the
+    n_zoom best seeds of round r-1 (order (E, index)) and scores, around each,
+    a 3^5 grid with the first grid's steps times 2^-r; the round's seeds are
+    numbered grid after grid in candidate order, row-major within a grid, and
+    every value is rounded once to float32 like any grid seed.  A seed met
+    again is scored again.  Returns the k best of all rounds in the order
+    (E, round, index): dict(seeds [k,5], E [k], round [k], index [k])."""
+    step0 = np.asarray(grid["step"], np.float32).reshape(5)
+    seeds = grid_values(grid)
+    E = scan(g, f, wire_id, drift, seeds, params, threads=threads)["E"]
+    best = [(E[i], 0, int(i), seeds[i]) for i in topk(E, k)]
+    for r in range(1, n_rounds):
+        step = (step0 * np.float32(2.0 ** -r)).astype(np.float32)
+        cand = topk(E, n_zoom)
+        seeds = np.concatenate([grid_values(_grid(seeds[c].astype(np.float32), step, (3, 3, 3, 3, 3)))
+                                for c in cand]) if len(cand) else np.zeros((0, 5))
+        E = scan(g, f, wire_id, drift, seeds, params, threads=threads)["E"] if len(seeds) else np.zeros(0)
+        best += [(E[i], r, int(i), seeds[i]) for i in topk(E, k)]
+    best.sort(key=lambda t: (t[0], t[1], t[2]))
+    best = best[:k]
+    return dict(seeds=np.array([b[3] for b in best]).reshape(-1, 5), E=np.array([b[0] for b in best]),
+                round=np.array([b[1] for b in best], np.int64), index=np.array([b[2] for b in best], np.int64))
+
+
+# --------------------------------------------------------------- event loop
+LOOP_SIGMA_Z0, LOOP_SIGMA_PZ0 = 26.0, 1.7   # resolution of the predicted (z0, pz0) [mm, MeV/c] (sec. 2.3)
+LOOP_MIN_HITS = 10                          # the loop stops below ten unclassified hits (sec. 2.3)
+LOOP_GRID_N = (5, 13, 5, 5, 13)             # neighbour grid: (z0, pz0) over +-3 sigma in sigma/2 steps,
+LOOP_TRANSVERSE_STEP = (0.002, 0.5, 0.5)    # (theta0, px0, py0) over +-2 fine steps
+UNCLASSIFIED = -128
+
+
+def neighbour_grid(seed, n=LOOP_GRID_N):
+    """Grid around a predicted seed of the neighbouring turn (sec. 2.3): n
+    points per axis at steps (0.002 rad, sigma_z0 / 2, 0.5, 0.5 MeV/c,
+    sigma_pz0 / 2)."""
+    return _grid(np.asarray(seed, np.float64).astype(np.float32),
+                 (LOOP_TRANSVERSE_STEP[0], LOOP_SIGMA_Z0 / 2, LOOP_TRANSVERSE_STEP[1], LOOP_TRANSVERSE_STEP[2],
+                  LOOP_SIGMA_PZ0 / 2), n)
+
+
+def event_loop(g, f, wire_id, drift, first_grid, params: ScanParams, k=8, n_rounds=10, n_zoom=4, n_iter=5,
+               sigma=0.2, max_turns=8, min_hits=LOOP_MIN_HITS, grid_n=LOOP_GRID_N, threads=None,
+               return_margin=False):
+    """Sec. 2.3, Fig. 7: the hits of one event classified into turns, in FP64.
+    A turn is found by the repeated scan (zoom_scan, one partition) of the hits
+    not yet classified; its hits are those the best seed classifies into
+    partition 0 (at least min_hits, else no turn).  The best seed is refined by
+    Gauss-Newton (n_iter iterations, the classification at the best seed held)
+    and the refined seed kept only where chi^2 went down.  From a turn's seed
+    the neighbouring turn's seed is predicted (extrapolate_turn) backwards
+    (-1) and forwards (+1) and searched on neighbour_grid (grid_n points per
+    axis); each direction
+    stops when the prediction leaves the chamber, when fewer than min_hits
+    hits remain or a scan classifies fewer, or after max_turns turns.
+    Returns (labels int32[H]: turn relative to the first one found, or
+    UNCLASSIFIED; seeds: turn -> float64[5]), and with return_margin the
+    smallest distance [mm] of each hit's |residual| to a classification cut
+    over the turn scans that classified it (inf if none did)."""
+    wid = np.asarray(wire_id, np.int32)
+    dr = np.asarray(drift, np.float64)
+    labels = np.full(wid.size, UNCLASSIFIED, np.int32)
+    margin = np.full(wid.size, np.inf)
+    p1 = ScanParams(params.h, params.max_steps, params.lam, 1, params.direction, params.charge)
+
+    def find_turn(grid):
+        idx = np.flatnonzero(labels == UNCLASSIFIED)
+        if idx.size < min_hits:
+            return None
+        w, d = wid[idx], dr[idx]
+        z = zoom_scan(g, f, w, d, grid, p1, k=k, n_rounds=n_rounds, n_zoom=n_zoom, threads=threads)
+        if z["E"].size == 0:
+            return None
+        best = z["seeds"][0]
+        cls = scan(g, f, w, d, best[None], p1, per_hit=True, threads=1)
+        part = cls["hit_part"][0]
+        margin[idx] = np.minimum(margin[idx], cls["hit_margin"][0])
+        found = idx[part == 0]
+        if found.size < min_hits:
+            return None
+        c0 = chi2(g, f, p1, w, d, part, best, sigma=sigma)[0]
+        so, c1, _, _, _ = refine(g, f, p1, w, d, part, best, n_iter=n_iter, sigma=sigma)
+        keep = bool(np.all(np.isfinite(so))) and c1 < c0
+        return found, (so if keep else best)
+
+    seeds = {}
+    first = find_turn(first_grid)
+    if first is None:
+        return (labels, seeds, margin) if return_margin else (labels, seeds)
+    labels[first[0]] = 0
+    seeds[0] = first[1]
+    for direction in (-1, 1):
+        cur, t = seeds[0], 0
+        while abs(t) < max_turns:
+            pred, status = extrapolate_turn(g, f, cur, p1, direction)
+            if status != 0:
+                break
+            turn = find_turn(neighbour_grid(pred, grid_n))
+            if turn is None:
+                break
+            t += direction
+            labels[turn[0]] = t
+            seeds[t] = cur = turn[1]
+    return (labels, seeds, margin) if return_margin else (labels, seeds)

@@ -34,11 +34,12 @@ def neighbour_grid(seed, n=(5, 13, 5, 5, 13), transverse_step=(0.002, 0.5, 0.5))
     return g
 
 
-def event_loop(tracker, wire_id, drift, first_grid, params, refine_params, max_turns=8, min_hits=MIN_HITS):
+def event_loop(tracker, wire_id, drift, first_grid, params, refine_params, max_turns=8, min_hits=MIN_HITS,
+               grid_n=(5, 13, 5, 5, 13)):
     """Classify the hits of one event into turns.  Returns (labels, seeds):
     labels[h] = turn index relative to the first turn found (0; -1 the turn
     before it, +1 the one after) or UNCLASSIFIED; seeds[k] = refined seed
-    (float32[5]) of turn k."""
+    (float32[5]) of turn k.  grid_n: points per axis of the neighbour grids."""
     torch = tracker.torch
     wid = np.asarray(wire_id, np.int32)
     dr = np.asarray(drift, np.float32)
@@ -84,7 +85,7 @@ def event_loop(tracker, wire_id, drift, first_grid, params, refine_params, max_t
             pred, status = tracker.extrapolate_turn(cur, p1, direction)
             if int(status[0]) != 0:
                 break
-            turn = find_turn(neighbour_grid(pred[0].cpu().numpy()))
+            turn = find_turn(neighbour_grid(pred[0].cpu().numpy(), n=grid_n))
             if turn is None:
                 break
             k += direction

@@ -28,8 +28,18 @@ def _edit(path, old, new):
     path.write_text(s.replace(old, new, 1))
 
 
-def test_digest_of_the_tree_is_the_recorded_one():
-    assert bench.csrc_digest() == bench.TRAFFIC["csrc_sha256"] == bench.FP32_COUNTS["csrc_sha256"]
+def test_recorded_counters_are_current_or_absent():
+    """Every recorded ncu figure was taken on the current scan-kernel sources,
+    or none is recorded (the line then reports null)."""
+    d = bench.csrc_digest()
+    for entry in list(bench.TRAFFIC.values()) + [bench.FP32_COUNTS]:
+        assert entry["csrc_sha256"] in (d, None)
+        assert bench.recorded(entry) is (entry if entry["csrc_sha256"] == d else None)
+
+
+def test_stale_records_are_not_reported():
+    assert bench.recorded({"bytes": 1, "csrc_sha256": "0" * 64}) is None
+    assert bench.recorded(None) is None
 
 
 def test_comments_whitespace_and_other_units_keep_the_digest(tmp_path, monkeypatch):
