@@ -298,7 +298,6 @@ struct SeedRecord {
     int round, index, nf, pad;
     uint32_t key[CDC_MAX_FOUND];
     float r[CDC_MAX_FOUND];
-    float cd[CDC_MAX_FOUND];
 };
 
 // Row-major index of the q-th seed of a grid in scan order: (z0, pz0)

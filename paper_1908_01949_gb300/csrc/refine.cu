@@ -830,10 +830,14 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
             if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
         flags |= T.flags;
         A.n = 0;
-        for (int q = 0; q < T.nf; ++q) {
+        for (int q = 0; q < T.nf; ++q) {  // each wire once, at its first entry
+            const int w = key_wire(FL.key[q]);
+            bool first = true;
+            for (int j = 0; j < q; ++j) first &= key_wire(FL.key[j]) != w;
+            if (!first) continue;
             int part;
-            entry_class(FL.key[q], FL.r[q], FL.cd[q], P.lam, part);
-            if (part >= 0) A.key[A.n++] = (uint32_t)key_wire(FL.key[q]) | ((uint32_t)part << 16);
+            record_class(FL.key, FL.r, T.nf, w, P.lam, part);
+            if (part >= 0) A.key[A.n++] = (uint32_t)w | ((uint32_t)part << 16);
         }
     }
     for (int q = 1; q < A.n; ++q) {  // sort by wire

@@ -279,7 +279,6 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                             for (int i = 0; i < T.nf; ++i) {
                                 R.key[i] = FL.key[i];
                                 R.r[i] = FL.r[i];
-                                R.cd[i] = FL.cd[i];
                             }
                         }
                     }
@@ -500,7 +499,6 @@ __global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, S
                 for (int i = lane; i < T.nf; i += 32) {
                     R.key[i] = wr->key[i];
                     R.r[i] = wr->r[i];
-                    R.cd[i] = wr->cd[i];
                 }
             }
             __syncwarp();  // the record is read before the next seed overwrites it
@@ -565,10 +563,8 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
             const SeedRecord& R = recs[(size_t)e * REC_SLOTS + slot];
             for (int h = h0 + lane; h < h1; h += 32) {
                 const int w = wire_id[h];
-                int part = -1;
-                float r2 = P.lam;
-                for (int i = 0; i < R.nf; ++i)
-                    if (key_wire(R.key[i]) == w) r2 = entry_class(R.key[i], R.r[i], R.cd[i], P.lam, part);
+                int part;
+                const float r2 = record_class(R.key, R.r, R.nf, w, P.lam, part);
                 if (hit_part) hit_part[h] = (int8_t)part;
                 if (hit_res2) hit_res2[h] = r2;
             }
@@ -581,10 +577,8 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
     T.run(G, F, P, s_lay, s_tab);
     for (int h = h0 + lane; h < h1; h += 32) {
         const int w = wire_id[h];
-        int part = -1;
-        float r2 = P.lam;
-        for (int i = 0; i < T.nf; ++i)
-            if (key_wire(rec->key[i]) == w) r2 = entry_class(rec->key[i], rec->r[i], rec->cd[i], P.lam, part);
+        int part;
+        const float r2 = record_class(rec->key, rec->r, T.nf, w, P.lam, part);
         if (hit_part) hit_part[h] = (int8_t)part;
         if (hit_res2) hit_res2[h] = r2;
     }

@@ -31,9 +31,8 @@
 // min((|DCA_k| - drift)^2, lambda) over the partitions k.  A minimum closer than
 // drift - sqrt(lambda) therefore removes its partition from the wire's term,
 // and a minimum farther than drift + sqrt(lambda) never matters.  The record
-// keeps, per wire with a minimum closer than drift + sqrt(lambda), the signed
-// residual of the current partition's DCA and the best term of the earlier
-// partitions (minima arrive in track order, so partitions only grow).
+// keeps one entry per (wire, partition) with a minimum closer than drift +
+// sqrt(lambda): the signed residual of that partition's DCA so far.
 //
 // Layout: every scalar of the tracer lives in registers; the list lives in
 // shared memory ([LIST_CAP][block] layout), the per-seed record (written a few
@@ -47,51 +46,38 @@ namespace cdc {
 constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
-// Record of one seed, one entry per wire that has a distance minimum closer
-// than drift + sqrt(lambda): key = wire | pc << 16 | pd << 20; r = DCA - drift
-// of partition pc so far (-inf once a minimum of pc is known to lie closer
-// than drift - sqrt(lambda)); cd = min(res^2, lambda) of the best earlier
-// partition pd (lambda: none).
+// Record of one seed: one entry per (wire, partition) with a distance minimum
+// closer than drift + sqrt(lambda), key = wire | partition << 16 and r = DCA -
+// drift of that partition so far (-inf once a minimum of it is known to lie
+// closer than drift - sqrt(lambda)).  Entries of one wire appear in partition
+// order (minima arrive in track order).
 struct FoundList {
     uint32_t key[CDC_MAX_FOUND];
     float r[CDC_MAX_FOUND];
-    float cd[CDC_MAX_FOUND];
 };
 
 __device__ __forceinline__ int key_wire(uint32_t k) { return (int)(k & 0xffffu); }
-__device__ __forceinline__ int key_pc(uint32_t k) { return (int)((k >> 16) & 0xfu); }
-__device__ __forceinline__ int key_pd(uint32_t k) { return (int)((k >> 20) & 0xfu); }
+__device__ __forceinline__ int key_part(uint32_t k) { return (int)(k >> 16); }
 
-// Eq. 1 term of a record entry: the best of the earlier partitions and the
-// current one.
-__device__ __forceinline__ float entry_term(float r, float cd, float lam) { return fminf(cd, fminf(r * r, lam)); }
+// Eq. 1 term of one partition's signed residual.
+__device__ __forceinline__ float part_term(float r, float lam) { return fminf(r * r, lam); }
 
-// A minimum of partition pt >= pc with signed residual r joins the entry:
-// within pc the DCA is the smaller distance; a later partition first folds
-// pc's term into (cd, pd).
-__device__ __forceinline__ void entry_merge(uint32_t& key, float& rc, float& cd, int pt, float r, float lam) {
-    const int pc = key_pc(key);
-    if (pt == pc) {
-        rc = fminf(rc, r);
-        return;
-    }
-    const float cc = fminf(rc * rc, lam);
-    if (cc < cd) {
-        cd = cc;
-        key = (key & ~(0xfu << 20)) | ((uint32_t)pc << 20);
-    }
-    key = (key & ~(0xfu << 16)) | ((uint32_t)pt << 16);
-    rc = r;
-}
-
-// Hit classification of a record entry (sec. 2.2: d^2 < lambda): the
+// Hit classification of `wire` from a record (sec. 2.2: d^2 < lambda): the
 // partition of the smallest term, ties to the lower partition, or -1; returns
-// the term.
-__device__ __forceinline__ float entry_class(uint32_t key, float rc, float cd, float lam, int& part) {
-    const float cc = fminf(rc * rc, lam);
-    const float b = fminf(cd, cc);
-    part = b < lam ? (cd <= cc ? key_pd(key) : key_pc(key)) : -1;
-    return b;
+// the term (lambda when the record has no entry of the wire).
+__device__ __forceinline__ float record_class(const uint32_t* key, const float* r, int n, int wire, float lam,
+                                              int& part) {
+    float best = lam;
+    part = -1;
+    for (int i = 0; i < n; ++i)
+        if (key_wire(key[i]) == wire) {
+            const float c = part_term(r[i], lam);
+            if (c < best) {
+                best = c;
+                part = key_part(key[i]);
+            }
+        }
+    return best;
 }
 
 // Fired cells of layer L in the search window (half widths band [mm] in
@@ -290,32 +276,35 @@ struct Tracer {
     uint32_t flags;
 
     // A distance minimum of `wire` in partition pt with signed residual r =
-    // D - drift; Eq. 1 accumulates the change of the wire's term on top of
-    // H lambda.  Minima with D >= drift + sqrt(lambda) never lower a term.
+    // D - drift; Eq. 1 accumulates the change of the wire's term (the smallest
+    // over its partitions) on top of H lambda.  Minima with D >= drift +
+    // sqrt(lambda) never lower a term.
     __device__ __forceinline__ void found(const ScanConst& P, FoundList& FL, int wire, int pt, float r) {
         if (!(r < P.sqrt_lam)) return;
         const unsigned long long bit = 1ull << (wire & 63);
+        float other = P.lam, cur = INFINITY;  // best term of the wire's other partitions; pt's residual so far
+        int at = -1;
         if (bloom & bit) {
             for (int i = 0; i < nf; ++i) {
-                uint32_t k = FL.key[i];
+                const uint32_t k = FL.key[i];
                 if (key_wire(k) == wire) {
-                    float rc = FL.r[i], cd = FL.cd[i];
-                    const float old = entry_term(rc, cd, P.lam);
-                    entry_merge(k, rc, cd, pt, r, P.lam);
-                    eacc += entry_term(rc, cd, P.lam) - old;
-                    FL.key[i] = k;
-                    FL.r[i] = rc;
-                    FL.cd[i] = cd;
-                    return;
+                    if (key_part(k) == pt) {
+                        at = i;
+                        cur = FL.r[i];
+                    } else {
+                        other = fminf(other, part_term(FL.r[i], P.lam));
+                    }
                 }
             }
         }
         bloom |= bit;
-        eacc += fminf(r * r, P.lam) - P.lam;
-        if (nf < CDC_MAX_FOUND) {
+        const float rn = fminf(cur, r);
+        eacc += fminf(other, part_term(rn, P.lam)) - fminf(other, part_term(cur, P.lam));
+        if (at >= 0) {
+            FL.r[at] = rn;
+        } else if (nf < CDC_MAX_FOUND) {
             FL.key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
             FL.r[nf] = r;
-            FL.cd[nf] = P.lam;
             ++nf;
         } else {
             flags |= CDC_FLAG_FOUND_OVERFLOW;

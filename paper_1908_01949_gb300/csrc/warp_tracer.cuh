@@ -28,7 +28,6 @@ constexpr int WIN_CAP = 128;       // fired wires of one window kept in shared m
 struct WarpFound {
     uint32_t key[CDC_MAX_FOUND];
     float r[CDC_MAX_FOUND];
-    float cd[CDC_MAX_FOUND];
     uint32_t win[WIN_CAP];
 };
 
@@ -138,35 +137,38 @@ struct WarpTracer {
     }
 
     // A distance minimum of `wire` in partition pt with signed residual r
-    // (arguments equal on all lanes): the rules of Tracer::found.
+    // (arguments equal on all lanes): the rules of Tracer::found, the record
+    // searched by all lanes at once.
     __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r) {
         if (!(r < P.sqrt_lam)) return;
+        float other = P.lam;
+        int at = -1;
         for (int b = 0; b < nf; b += 32) {
             const int i = b + lane;
-            const unsigned m = __ballot_sync(WARP_ALL, i < nf && key_wire(rec->key[i]) == wire);
-            if (m) {
-                const int k = b + __ffs(m) - 1;
-                uint32_t key = rec->key[k];
-                float rc = rec->r[k], cd = rec->cd[k];
-                __syncwarp();
-                const float old = entry_term(rc, cd, P.lam);
-                entry_merge(key, rc, cd, pt, r, P.lam);
-                eacc += entry_term(rc, cd, P.lam) - old;
-                if (lane == 0) {
-                    rec->key[k] = key;
-                    rec->r[k] = rc;
-                    rec->cd[k] = cd;
+            bool same = false;
+            if (i < nf) {
+                const uint32_t k = rec->key[i];
+                if (key_wire(k) == wire) {
+                    if (key_part(k) == pt)
+                        same = true;
+                    else
+                        other = fminf(other, part_term(rec->r[i], P.lam));
                 }
-                __syncwarp();
-                return;
             }
+            const unsigned m = __ballot_sync(WARP_ALL, same);
+            if (m) at = b + __ffs(m) - 1;
         }
-        eacc += fminf(r * r, P.lam) - P.lam;
-        if (nf < CDC_MAX_FOUND) {
+        for (int o = 16; o > 0; o >>= 1) other = fminf(other, __shfl_xor_sync(WARP_ALL, other, o));
+        const float cur = at >= 0 ? rec->r[at] : INFINITY;
+        __syncwarp();
+        const float rn = fminf(cur, r);
+        eacc += fminf(other, part_term(rn, P.lam)) - fminf(other, part_term(cur, P.lam));
+        if (at >= 0) {
+            if (lane == 0) rec->r[at] = rn;
+        } else if (nf < CDC_MAX_FOUND) {
             if (lane == 0) {
                 rec->key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
                 rec->r[nf] = r;
-                rec->cd[nf] = P.lam;
             }
             ++nf;
         } else {
