@@ -237,19 +237,43 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
     const int lane = threadIdx.x & 31;
     Tracer<KIND> T;
     FoundList FL;
-    long long my = -1;  // -1: wants a seed, -2: no seeds left
+    long long my = -1;   // this lane's seed; -1: ended (or none yet), -2: no seeds left
+    long long done = -1; // an ended seed whose score is still to be formed
     int ev = 0;
     unsigned long long nsteps = 0;
     for (;;) {
-        unsigned need = __ballot_sync(FULL, my == -1);
-        if ((need | __ballot_sync(FULL, my == -2)) != FULL) need = 0;  // refill whole cohorts only
-        if (need) {
-            int leader = __ffs(need) - 1;
+        if (__all_sync(FULL, my < 0)) {
+            // the cohort ended: its seeds' scores are formed from their records
+            // together (converged), then whole cohorts are refilled
+            if (done >= 0) {
+                const int H = io.hit_off[ev + 1] - io.hit_off[ev];
+                const float score = T.score(P, H, FL);
+                io.E[done] = score;
+                if (io.recs) {
+                    const int slot = record_slot(io, ev, score);
+                    if (slot >= 0) {
+                        SeedRecord& R = io.recs[(size_t)ev * REC_SLOTS + slot];
+                        R.round = io.round;
+                        R.index = (int)(done - io.seed_off[ev]);
+                        R.nf = T.nf;
+                        for (int i = 0; i < T.nf; ++i) {
+                            R.key[i] = FL.key[i];
+                            R.r[i] = FL.r[i];
+                        }
+                    }
+                }
+                if (T.flags) atomicOr(&io.flags[ev], T.flags);
+                nsteps += (unsigned long long)T.n;
+                done = -1;
+            }
+            const unsigned need = __ballot_sync(FULL, my == -1);
+            if (!need) break;
+            const int leader = __ffs(need) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(&io.counters[0], (unsigned long long)__popc(need));
             base = __shfl_sync(FULL, base, leader);
             if (my == -1) {
-                long long s = (long long)base + __popc(need & ((1u << lane) - 1u));
+                const long long s = (long long)base + __popc(need & ((1u << lane) - 1u));
                 if (s < total) {
                     ev = find_event(io.seed_off, io.n_events, s);
                     float sd[5];
@@ -262,28 +286,10 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                 }
             }
         }
-        if (__all_sync(FULL, my == -2)) break;
         if (my >= 0) {
             for (int it = 0; it < CHUNK; ++it) {
                 if (!T.step(G, F, P, s_lay, s_tab, FL)) {
-                    int H = io.hit_off[ev + 1] - io.hit_off[ev];
-                    const float score = T.score(P, H);
-                    io.E[my] = score;
-                    if (io.recs) {
-                        const int slot = record_slot(io, ev, score);
-                        if (slot >= 0) {
-                            SeedRecord& R = io.recs[(size_t)ev * REC_SLOTS + slot];
-                            R.round = io.round;
-                            R.index = (int)(my - io.seed_off[ev]);
-                            R.nf = T.nf;
-                            for (int i = 0; i < T.nf; ++i) {
-                                R.key[i] = FL.key[i];
-                                R.r[i] = FL.r[i];
-                            }
-                        }
-                    }
-                    if (T.flags) atomicOr(&io.flags[ev], T.flags);
-                    nsteps += (unsigned long long)T.n;
+                    done = my;
                     my = -1;
                     break;
                 }

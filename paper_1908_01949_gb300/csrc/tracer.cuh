@@ -30,9 +30,10 @@
 // all minima inside that partition, and the wire's term is the smallest
 // min((|DCA_k| - drift)^2, lambda) over the partitions k.  A minimum closer than
 // drift - sqrt(lambda) therefore removes its partition from the wire's term,
-// and a minimum farther than drift + sqrt(lambda) never matters.  The record
-// keeps one entry per (wire, partition) with a minimum closer than drift +
-// sqrt(lambda): the signed residual of that partition's DCA so far.
+// and a minimum farther than drift + sqrt(lambda) never matters.  While it
+// steps, the tracer only appends each minimum that can matter to the seed's
+// record (a few instructions, however divergent); the terms and their sum
+// are formed from the record once the seed has ended (record_score).
 //
 // Layout: every scalar of the tracer lives in registers; the list lives in
 // shared memory ([LIST_CAP][block] layout), the per-seed record (written a few
@@ -46,11 +47,10 @@ namespace cdc {
 constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
-// Record of one seed: one entry per (wire, partition) with a distance minimum
-// closer than drift + sqrt(lambda), key = wire | partition << 16 and r = DCA -
-// drift of that partition so far (-inf once a minimum of it is known to lie
-// closer than drift - sqrt(lambda)).  Entries of one wire appear in partition
-// order (minima arrive in track order).
+// Record of one seed: every distance minimum closer than drift + sqrt(lambda),
+// in track order (so partitions never decrease along it), as key = wire |
+// partition << 16 and r = D - drift (-inf where cheap bounds put D below
+// drift - sqrt(lambda)).
 struct FoundList {
     uint32_t key[CDC_MAX_FOUND];
     float r[CDC_MAX_FOUND];
@@ -62,22 +62,61 @@ __device__ __forceinline__ int key_part(uint32_t k) { return (int)(k >> 16); }
 // Eq. 1 term of one partition's signed residual.
 __device__ __forceinline__ float part_term(float r, float lam) { return fminf(r * r, lam); }
 
+// Term of `wire` from entries i0.. of a record (i0: its first entry): per
+// partition the nearest minimum (smallest residual), then the smallest term
+// over the partitions, ties to the lower partition; part = its partition, or
+// -1 when the term is lambda.
+__device__ __forceinline__ float wire_term(const uint32_t* key, const float* r, int n, int i0, int wire, float lam,
+                                           int& part) {
+    float best = lam, cm = r[i0];
+    int cp = key_part(key[i0]);
+    part = -1;
+    for (int j = i0 + 1; j < n; ++j) {
+        if (key_wire(key[j]) != wire) continue;
+        const int pj = key_part(key[j]);
+        if (pj == cp) {
+            cm = fminf(cm, r[j]);
+        } else {
+            const float t = part_term(cm, lam);
+            if (t < best) {
+                best = t;
+                part = cp;
+            }
+            cp = pj;
+            cm = r[j];
+        }
+    }
+    const float t = part_term(cm, lam);
+    if (t < best) {
+        best = t;
+        part = cp;
+    }
+    return best;
+}
+
+// Eq. 1 of a seed from its record: H lambda plus, per wire, its term minus
+// lambda, summed in the order of the wires' first entries.
+__device__ __forceinline__ float record_score(const uint32_t* key, const float* r, int n, float lam, int H) {
+    float e = 0.f;
+    for (int i = 0; i < n; ++i) {
+        const int w = key_wire(key[i]);
+        bool first = true;
+        for (int j = 0; j < i; ++j) first &= key_wire(key[j]) != w;
+        if (!first) continue;
+        int part;
+        e += wire_term(key, r, n, i, w, lam, part) - lam;
+    }
+    return fmaf((float)H, lam, e);
+}
+
 // Hit classification of `wire` from a record (sec. 2.2: d^2 < lambda): the
-// partition of the smallest term, ties to the lower partition, or -1; returns
-// the term (lambda when the record has no entry of the wire).
+// partition of its term, or -1; returns the term (lambda without entries).
 __device__ __forceinline__ float record_class(const uint32_t* key, const float* r, int n, int wire, float lam,
                                               int& part) {
-    float best = lam;
     part = -1;
     for (int i = 0; i < n; ++i)
-        if (key_wire(key[i]) == wire) {
-            const float c = part_term(r[i], lam);
-            if (c < best) {
-                best = c;
-                part = key_part(key[i]);
-            }
-        }
-    return best;
+        if (key_wire(key[i]) == wire) return wire_term(key, r, n, i, wire, lam, part);
+    return lam;
 }
 
 // Fired cells of layer L in the search window (half widths band [mm] in
@@ -271,38 +310,14 @@ struct Tracer {
     int stride;
     int n, part, nf, nc;
     bool outside, over;
-    float eacc;
-    unsigned long long bloom;
     uint32_t flags;
 
     // A distance minimum of `wire` in partition pt with signed residual r =
-    // D - drift; Eq. 1 accumulates the change of the wire's term (the smallest
-    // over its partitions) on top of H lambda.  Minima with D >= drift +
-    // sqrt(lambda) never lower a term.
+    // D - drift, appended to the record if it can matter (D < drift +
+    // sqrt(lambda)).
     __device__ __forceinline__ void found(const ScanConst& P, FoundList& FL, int wire, int pt, float r) {
         if (!(r < P.sqrt_lam)) return;
-        const unsigned long long bit = 1ull << (wire & 63);
-        float other = P.lam, cur = INFINITY;  // best term of the wire's other partitions; pt's residual so far
-        int at = -1;
-        if (bloom & bit) {
-            for (int i = 0; i < nf; ++i) {
-                const uint32_t k = FL.key[i];
-                if (key_wire(k) == wire) {
-                    if (key_part(k) == pt) {
-                        at = i;
-                        cur = FL.r[i];
-                    } else {
-                        other = fminf(other, part_term(FL.r[i], P.lam));
-                    }
-                }
-            }
-        }
-        bloom |= bit;
-        const float rn = fminf(cur, r);
-        eacc += fminf(other, part_term(rn, P.lam)) - fminf(other, part_term(cur, P.lam));
-        if (at >= 0) {
-            FL.r[at] = rn;
-        } else if (nf < CDC_MAX_FOUND) {
+        if (nf < CDC_MAX_FOUND) {
             FL.key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
             FL.r[nf] = r;
             ++nf;
@@ -377,8 +392,6 @@ struct Tracer {
         nc = 0;
         outside = true;
         over = false;
-        eacc = 0.f;
-        bloom = 0ull;
         flags = 0u;
         // start of the track: a minimum if the distance grows from there
         const float x = s.rx, y = s.ry, z = s.rz, tx = s.tx, ty = s.ty, tz = s.tz;
@@ -484,7 +497,9 @@ struct Tracer {
         return finish(G, P, s_lay, s_tab, FL);
     }
 
-    __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
+    __device__ __forceinline__ float score(const ScanConst& P, int H, const FoundList& FL) const {
+        return record_score(FL.key, FL.r, nf, P.lam, H);
+    }
 };
 
 }  // namespace cdc

@@ -117,7 +117,6 @@ struct WarpTracer {
     float c_g, c_d, c_cosa;
     int n, part, nf, nc, lane;
     bool outside, over;
-    float eacc;
     uint32_t flags;
 
     // Entry j of the window gathered into rec->win (tot wires): (wire, cosa),
@@ -137,35 +136,11 @@ struct WarpTracer {
     }
 
     // A distance minimum of `wire` in partition pt with signed residual r
-    // (arguments equal on all lanes): the rules of Tracer::found, the record
-    // searched by all lanes at once.
+    // (arguments equal on all lanes), appended to the record as by
+    // Tracer::found.
     __device__ __forceinline__ void found(const ScanConst& P, int wire, int pt, float r) {
         if (!(r < P.sqrt_lam)) return;
-        float other = P.lam;
-        int at = -1;
-        for (int b = 0; b < nf; b += 32) {
-            const int i = b + lane;
-            bool same = false;
-            if (i < nf) {
-                const uint32_t k = rec->key[i];
-                if (key_wire(k) == wire) {
-                    if (key_part(k) == pt)
-                        same = true;
-                    else
-                        other = fminf(other, part_term(rec->r[i], P.lam));
-                }
-            }
-            const unsigned m = __ballot_sync(WARP_ALL, same);
-            if (m) at = b + __ffs(m) - 1;
-        }
-        for (int o = 16; o > 0; o >>= 1) other = fminf(other, __shfl_xor_sync(WARP_ALL, other, o));
-        const float cur = at >= 0 ? rec->r[at] : INFINITY;
-        __syncwarp();
-        const float rn = fminf(cur, r);
-        eacc += fminf(other, part_term(rn, P.lam)) - fminf(other, part_term(cur, P.lam));
-        if (at >= 0) {
-            if (lane == 0) rec->r[at] = rn;
-        } else if (nf < CDC_MAX_FOUND) {
+        if (nf < CDC_MAX_FOUND) {
             if (lane == 0) {
                 rec->key[nf] = (uint32_t)wire | ((uint32_t)pt << 16);
                 rec->r[nf] = r;
@@ -174,7 +149,6 @@ struct WarpTracer {
         } else {
             flags |= CDC_FLAG_FOUND_OVERFLOW;
         }
-        __syncwarp();
     }
 
     // Minima found by the lanes (signed residuals; +inf where none), recorded
@@ -259,7 +233,6 @@ struct WarpTracer {
         nc = 0;
         outside = true;
         over = false;
-        eacc = 0.f;
         flags = 0u;
         c_wire = 0;
         c_W = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -394,7 +367,11 @@ struct WarpTracer {
         }
     }
 
-    __device__ __forceinline__ float score(const ScanConst& P, int H) const { return fmaf((float)H, P.lam, eacc); }
+    // Eq. 1 of the seed from its record (every lane the same value).
+    __device__ __forceinline__ float score(const ScanConst& P, int H) const {
+        __syncwarp();
+        return record_score(rec->key, rec->r, nf, P.lam, H);
+    }
 };
 
 }  // namespace cdc
