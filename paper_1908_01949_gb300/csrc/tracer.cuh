@@ -152,10 +152,12 @@ __device__ __forceinline__ bool layer_cells(const DevLayer& L, const uint32_t* f
 template <class Fn>
 __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2* s_tab, const float* dtab,
                                              const uint32_t* fired, float max_drift, float band, float d_win,
-                                             float rho, float phi, float z, Fn&& fn) {
+                                             float rho, float phi, float z, Fn&& fn, float rlo = -1.f,
+                                             float rhi = -1.f) {
     const uchar2 lr = s_tab[min((int)rho, TAB_N - 1)];
     if (lr.x > lr.y) return;
-    const float blo = fmaxf(rho - band, 0.f), bhi = rho + band;
+    // radial band: rho +- band, or [rlo - band, rhi + band] where the caller bounds the radii ahead
+    const float blo = fmaxf((rlo >= 0.f ? rlo : rho) - band, 0.f), bhi = (rhi >= 0.f ? rhi : rho) + band;
     const float blo2 = blo * blo, bhi2 = bhi * bhi, z2 = z * z;
     for (int l = lr.x; l <= lr.y; ++l) {
         const DevLayer& L = s_lay[l];
@@ -346,7 +348,18 @@ struct Tracer {
         const float reach = wide + 0.5f;
         const float kap = fabsf(s.lam) * P.b_max;
         const float bend = fmaf(0.5f * kap, reach * reach, 0.01f);
-        visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band + wide, P.d_win + wide, rho, atan2f(y, x), z,
+        // Radii the track can reach within the next LIST_M segments (arc s <= wide):
+        // with q = rho^2, q' = 2 (x tx + y ty) and q'' = 2 (tx^2 + ty^2) + 2 (x, y) .
+        // (tx', ty') in [-2 (rho + s) kap, 2 + 2 (rho + s) kap], q stays between the
+        // end values of q0 + q'0 s - (rho + wide) kap s^2 and q0 + q'0 s + (1 + (rho +
+        // wide) kap) s^2 (a concave and a convex quadratic), and |rho(s) - rho| <= s.
+        // The window takes those radii +- the band (0.01 mm to spare) instead of
+        // rho +- (band + wide): the layers behind the track drop out.
+        const float q0 = rho * rho, dq = 2.0f * wide * fmaf(x, tx, y * ty), ck = (rho + wide) * kap * wide * wide;
+        const float qlo = fminf(q0, dq + q0 - ck), qhi = fmaxf(q0, dq + q0 + fmaf(wide, wide, ck));
+        const float rlo = fmaxf(fmaxf(sqrtf(fmaxf(qlo, 0.f)) - 0.01f, rho - wide), 0.f);
+        const float rhi = fminf(sqrtf(qhi) + 0.01f, rho + wide);
+        visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win + wide, rho, atan2f(y, x), z,
                      [&](int wire, float d, float cosa) {
                          const float4 W = __ldg(G.wires + wire);
                          float tp2;
@@ -362,7 +375,8 @@ struct Tracer {
                                     fmaf(wp2, tp2, -g * g) <= lim * lim * tp2;
                          }
                          if (keep && !sink(wire, g, d, cosa)) over = true;
-                     });
+                     },
+                     rlo, rhi);
     }
 
     // Per-lane candidate list in this thread's column.
