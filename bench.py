@@ -25,8 +25,11 @@ Legs (timed separately, reported beside the headline):
     batched Hough, and the FP32 steppers against the FP64 GPU stepper to 6 m;
   bidirectional, split_ab, event_loop: the ranked extensions.
 
---profile-case runs only the multi-turn leg on a 240000-seed coarse grid for
-profiler captures; its line is marked as such and is not a benchmark result.
+--profile-case runs only the multi-turn leg on a 240000-seed coarse grid, and
+--profile-batched N one eager call of the batched step on its first N events
+(fixed launch shape, no autotuning, so that the first scan-kernel launch is
+that call's coarse round), for profiler captures; their lines are marked as
+such and are not benchmark results.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 a bounded sample of the headline workload instead.
@@ -471,8 +474,8 @@ def headline_batched(args, ws, rank, local, dist, g, fm, flush, sampler, peak):
     # classification quality (sec. 3.1, Eqs. 2-3): the grids are centred on the first turn, so scan partition k
     # is truth turn k
     truth = torch.as_tensor(np.concatenate([e.truth_part for e in evs]).astype(np.int8), device=dev)
-    cls_counts = tr.classification_counts(off_t, out["hit_part"], truth, MAX_PART).cpu().numpy()
-    eps, pur = cdc.efficiency_purity(cls_counts)
+    cls_counts = tr.classification_counts(off_t, out["hit_part"], truth, MAX_PART)
+    eps, pur = (x.cpu().numpy() for x in tr.efficiency_purity(cls_counts))
     return {
         "ms": ms, "seeds_step": seeds_step, "rkn_step": rkn_step, "clocks": clocks, "n_events": n_ev,
         "launches_per_step": launches_per_step,
@@ -495,6 +498,41 @@ def headline_batched(args, ws, rank, local, dist, g, fm, flush, sampler, peak):
                                                     "turn k"}},
         "workload": {"evs": evs, "grids": grids, "counts": counts},
     }
+
+
+def profile_batched(args, local, g, fm, flush):
+    """One eager call of the batched step on its first N events, at a fixed
+    launch shape (no autotuning): the call's first scan-kernel launch is its
+    coarse round, the launch a profiler capture takes (-k scan_kernel -c 1)."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    n_ev = int(args.profile_batched)
+    evs, grids, S = make_batched_workload(n_ev)
+    n = int(sum(int(np.prod(gr["n"])) for gr in grids))
+    off, wid, dr = S.pack_events(evs)
+    tr = cdc.Tracker(g, fm, device=local, max_events=n_ev, max_seeds=n, max_hits=int(wid.size))
+    tr.ctx.cdc_set_scan_config(*(tuple(int(x) for x in args.scan_shape.split(",")) if args.scan_shape else (256, 32)))
+    sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
+                         n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
+    off_t, wid_t, dr_t = tr.events_to_device(off, wid, dr)
+    gr_t = cdc.grids_to_tensor(grids, tr.dev)
+    tr.ctx.cdc_kernel_timer(1)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    out = tr.scan(off_t, wid_t, dr_t, gr_t, sp, want_hits=True)
+    t1.record()
+    torch.cuda.synchronize()
+    _, nl, per = tr.ctx.cdc_kernel_time()
+    tr.ctx.cdc_kernel_timer(0)
+    ms = t0.elapsed_time(t1)
+    seeds = n + (N_ROUNDS - 1) * N_ZOOM * 243 * n_ev
+    steps = out["steps"].cpu().numpy()
+    return {"events": n_ev, "coarse_seeds": n, "ms": ms, "seeds_per_s": seeds / (ms / 1e3),
+            "coarse_launch_ms": float(per[0]) if nl else None, "coarse_rkn_steps": float(steps[0]),
+            "rkn_steps": float(steps.sum())}
 
 
 def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
@@ -768,8 +806,8 @@ def bidirectional_leg(args, rank, local, g, fm, flush):
     keep = np.flatnonzero(nc >= NC_CUT)
     quality = {}
     for name, o in zip(("entrance", "exit"), outs):
-        C = tr.classification_counts(off_t, o["hit_part"], truth_t, 8).cpu().numpy()
-        ep = np.array([[v[0] for v in cdc.efficiency_purity(C[e])] for e in keep]).reshape(-1, 2)
+        C = tr.classification_counts(off_t, o["hit_part"], truth_t, 8)
+        ep = np.array([[float(v[0]) for v in tr.efficiency_purity(C[e])] for e in keep]).reshape(-1, 2)
         quality[name] = {"efficiency_mean": float(np.nanmean(ep[:, 0])) if keep.size else None,
                          "purity_mean": float(np.nanmean(ep[:, 1])) if keep.size else None}
     return {"events": n_ev, "seeds_per_direction": n_seeds, "ms": ms, "events_per_s": n_ev / (ms / 1e3),
@@ -825,7 +863,7 @@ def event_loop_leg(args, rank, local, g, fm):
         counts += c[0].cpu().numpy()
         found.append(len(seeds))
     wall = time.perf_counter() - t0
-    eps, pur = cdc.efficiency_purity(counts)
+    eps, pur = (x.cpu().numpy() for x in tr.efficiency_purity(torch.as_tensor(counts.astype(np.int32), device=tr.dev)))
     return {"events": n_ev, "ms_per_event": 1e3 * wall / n_ev, "events_per_s": n_ev / wall,
             "turns_found_mean": float(np.mean(found)), "truth_turns_mean": float(np.mean([e.n_turns for e in evs])),
             "efficiency_per_turn": [None if np.isnan(x) else float(x) for x in eps],
@@ -1052,6 +1090,19 @@ def run_cuda(args, ws, rank, local):
     peak = fp32_peak(probe, sampler)
     stream = torch.cuda.current_stream()
 
+    if args.profile_batched:
+        pb = profile_batched(args, local, g, fm, flush)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": pb["seeds_per_s"], "unit": "seeds/s", "n_gpus": ws,
+                              "steps": 1, "warmup": 0, "ms_per_step": pb["ms"], "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                              "config": {"workload": WORKLOAD, "profile_case":
+                                         f"one eager call on the first {pb['events']} events of the batched step "
+                                         "for profiler captures, not a benchmark result"},
+                              "profile_batched": pb, "fp32_peak": peak}))
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.profile_case:
         mt = multi_turn_leg(args, ws, rank, local, g, fm, flush, peak)
         if rank == 0:
@@ -1283,6 +1334,8 @@ def main():
                     help="the same for the multi-turn throughput and end-to-end runs (default 0: one lane per seed)")
     ap.add_argument("--inflight", type=int, default=8,
                     help="distinct events in flight (one context and stream each) in the multi-turn leg")
+    ap.add_argument("--profile-batched", type=int, default=0, metavar="N",
+                    help="one eager call of the batched step on its first N events (profiler captures; not a result)")
     ap.add_argument("--profile-case", action="store_true",
                     help="only the multi-turn leg on a 240000-seed coarse grid (profiler captures; not a result)")
     args = ap.parse_args()

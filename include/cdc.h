@@ -37,7 +37,7 @@ extern "C" {
 #define CDC_MAX_K 64
 #define CDC_MAX_ZOOM 8
 #define CDC_MAX_ROUNDS 16
-#define CDC_MAX_FOUND 128 /* per-seed record: wires passed closer than drift + sqrt(lambda) */
+#define CDC_MAX_FOUND 256 /* per-seed record: passes of fired wires closer than drift + sqrt(lambda) */
 
 typedef struct cdc_ctx cdc_ctx;
 
@@ -53,7 +53,7 @@ typedef enum {
 
 /* Per-event warning flags (bitmask). */
 #define CDC_FLAG_STEP_CAP 1u        /* some seed stopped at max_steps */
-#define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed passed more than CDC_MAX_FOUND fired wires within drift + sqrt(lambda) */
+#define CDC_FLAG_FOUND_OVERFLOW 2u  /* a seed's record of passes (CDC_MAX_FOUND, compacted when full) or refined hits overflowed */
 #define CDC_FLAG_EMPTY 4u           /* no hits, no seeds, no Hough candidate, or grids beyond the reservation */
 #define CDC_FLAG_NOT_SPD 8u         /* refine: normal matrix regularised */
 #define CDC_FLAG_DOCA_ZERO 16u      /* refine: a hit at zero distance was left out */
@@ -369,6 +369,17 @@ int cdc_extrapolate_turn(cdc_ctx* ctx, int n_seeds, const float* seeds, const cd
  * n_part 1..16.  Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_CUDA. */
 int cdc_classification_counts(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int8_t* hit_part,
                               const int8_t* truth_part, int n_part, int32_t* counts, void* stream);
+
+/* Eqs. 2-3 of sec. 3.1 from classification counts: with C the element-wise
+ * sum of counts[0 .. n_sets - 1] (the layout cdc_classification_counts
+ * writes, [n_sets][n_part + 1][n_part + 1] int32, device), eff[j] =
+ * C_{j->j} / C_j (all hits of truth partition j, classified anywhere) and
+ * pur[j] = C_{j->j} / sum_{i >= 0} C_{i->j} (the signal's hits classified j),
+ * j = 0 .. n_part - 1, as float32 on the device (NaN where a denominator is 0).
+ * n_part 1..16, n_sets >= 1.  Asynchronous on `stream`.  Errors: CDC_ERR_ARG,
+ * CDC_ERR_RANGE, CDC_ERR_CUDA. */
+int cdc_efficiency_purity(cdc_ctx* ctx, int n_sets, const int32_t* counts, int n_part, float* eff, float* pur,
+                          void* stream);
 
 /* Hits found by both directions of the bidirectional scan (sec. 2.2: the scan
  * runs independently on seeds at the entrance and at the exit of a partition,

@@ -15,7 +15,7 @@ from ._lib import (CAND_DTYPE, CDC_MAX_K, CDC_MAX_ZOOM, EXPORTS, FLAG_BAD_HIT, F
                    FLAG_FOUND_OVERFLOW, FLAG_LOST_HIT, FLAG_NOT_SPD, FLAG_STEP_CAP, GRID_BYTES, GRID_DTYPE, CdcError,
                    Context, grids_to_tensor, hough_params, lib, refine_params, scan_params, tensor_to_grids)
 
-__all__ = ["Context", "Tracker", "CdcError", "chi2", "efficiency_purity", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
+__all__ = ["Context", "Tracker", "CdcError", "chi2", "scan_params", "hough_params", "refine_params", "grids_to_tensor",
            "tensor_to_grids", "GRID_DTYPE", "CAND_DTYPE", "EXPORTS", "lib"]
 
 
@@ -97,6 +97,18 @@ class Tracker:
         counts = t.empty((ne, n_part + 1, n_part + 1), dtype=t.int32, device=self.dev)
         self.ctx.cdc_classification_counts(ne, hit_off, hit_part, truth_part, n_part, counts, stream)
         return counts
+
+    def efficiency_purity(self, counts, stream=None):
+        """Eqs. 2-3 (sec. 3.1) from device counts [..., n+1, n+1] (as
+        classification_counts writes them), summed over the leading axes:
+        (eff [n], pur [n]) float32 device tensors, NaN for a zero denominator."""
+        t = self.torch
+        c = counts.reshape(-1, counts.shape[-2], counts.shape[-1]).contiguous()
+        n = int(c.shape[-1]) - 1
+        eff = t.empty(n, dtype=t.float32, device=self.dev)
+        pur = t.empty(n, dtype=t.float32, device=self.dev)
+        self.ctx.cdc_efficiency_purity(int(c.shape[0]), c, n, eff, pur, stream)
+        return eff, pur
 
     def extrapolate_turn(self, seeds, params, direction, stream=None):
         """Seeds of the previous (-1) or next (+1) turn partition (sec. 2.3):
@@ -185,19 +197,6 @@ def chi2(tracker, seed_event, seeds, hit_off, wire_id, drift, scan, params):
     may require grad); the hit assignment of each seed is taken at the seed
     itself, as in cdc_chi2_grad."""
     return _chi2_function().apply(seeds, tracker, seed_event, hit_off, wire_id, drift, scan, params)
-
-
-def efficiency_purity(counts):
-    """Eqs. 2-3 of sec. 3.1 from classification counts [..., n+1, n+1] (index
-    0 = -1): eps[j] = C_{j->j} / C_j and pi[j] = C_{j->j} / sum_{i>=0} C_{i->j},
-    summed over any leading (event) axes; NaN where a denominator is 0."""
-    c = np.asarray(counts, dtype=np.float64)
-    c = c.reshape(-1, c.shape[-2], c.shape[-1]).sum(0)
-    diag = np.diagonal(c)[1:]
-    with np.errstate(invalid="ignore", divide="ignore"):
-        eps = diag / c[1:, :].sum(1)
-        pur = diag / c[1:, 1:].sum(0)
-    return eps, pur
 
 
 def decode_candidates(t):

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcdc.so")
 CDC_MAX_K = 64
 CDC_MAX_ZOOM = 8
 CDC_MAX_ROUNDS = 16
-CDC_MAX_FOUND = 128
+CDC_MAX_FOUND = 256
 
 FLAG_STEP_CAP = 1
 FLAG_FOUND_OVERFLOW = 2
@@ -36,7 +36,7 @@ EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
            "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_extrapolate_turn", "cdc_classification_counts",
-           "cdc_common_hits", "cdc_fp32_peak",
+           "cdc_common_hits", "cdc_fp32_peak", "cdc_efficiency_purity",
            "cdc_scan_seeds_noalloc"]
 
 
@@ -123,6 +123,8 @@ def lib():
         L.cdc_get_scan_config.argtypes = [vp, P(cdc_scan_config)]
         L.cdc_tune_scan.argtypes = [vp, C.c_int, vp, vp, vp, vp, P(cdc_scan_params), C.c_int, P(cdc_scan_config),
                                     vp, vp]
+        L.cdc_fp32_peak.argtypes = [vp, C.c_int, P(C.c_double), P(C.c_double), vp]
+        L.cdc_efficiency_purity.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("cdc_destroy", "cdc_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -321,6 +323,13 @@ class Context:
             self.h, int(n_events), _dev(hit_off, torch.int32, "hit_off", d), _dev(hit_part, torch.int8, "hit_part", d),
             _dev(truth_part, torch.int8, "truth_part", d), int(n_part), _dev(counts, torch.int32, "counts", d),
             _stream(stream)))
+
+    def cdc_efficiency_purity(self, n_sets, counts, n_part, eff, pur, stream=None):
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_efficiency_purity(
+            self.h, int(n_sets), _dev(counts, torch.int32, "counts", d), int(n_part),
+            _dev(eff, torch.float32, "eff", d), _dev(pur, torch.float32, "pur", d), _stream(stream)))
 
     def cdc_extrapolate_turn(self, n_seeds, seeds, scan, direction, seeds_out, status, stream=None):
         import torch

@@ -476,6 +476,18 @@ int cdc_classification_counts(cdc_ctx* c, int n_events, const int32_t* hit_off, 
     return CDC_OK;
 }
 
+int cdc_efficiency_purity(cdc_ctx* c, int n_sets, const int32_t* counts, int n_part, float* eff, float* pur,
+                          void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (n_sets < 1) return fail(c, CDC_ERR_ARG, "n_sets < 1");
+    if (n_part < 1 || n_part > 16) return fail(c, CDC_ERR_RANGE, "n_part outside 1..16");
+    if (!counts || !eff || !pur) return fail(c, CDC_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_efficiency_purity(n_sets, counts, n_part, eff, pur, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "efficiency and purity");
+    return CDC_OK;
+}
+
 int cdc_reserve_split(cdc_ctx* c, int chunk, int max_steps) {
     if (!c) return CDC_ERR_ARG;
     if (chunk < 1 || chunk > (1 << 20) || max_steps < 1 || max_steps > 6900)

@@ -79,6 +79,8 @@ cudaError_t launch_extrapolate_turn(const DevGeom& G, const DevField& F, const S
 
 cudaError_t launch_class_counts(int n_events, const int32_t* hit_off, const int8_t* hit_part,
                                 const int8_t* truth_part, int n_part, int32_t* counts, int num_sms, cudaStream_t st);
+cudaError_t launch_efficiency_purity(int n_sets, const int32_t* counts, int n_part, float* eff, float* pur,
+                                     cudaStream_t st);
 
 cudaError_t launch_propagate(const DevGeom& G, const DevField& F, const ScanConst& P, int n_seeds,
                              const float* seeds, int every, int n_rec, int precision, double* pos, int32_t* n_steps,

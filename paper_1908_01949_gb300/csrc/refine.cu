@@ -26,6 +26,7 @@
 namespace cdc {
 
 constexpr int MAX_CK = 64;      // checkpoints per seed
+constexpr int MAX_ASSIGNED = 128;  // classified hits refined per seed (more: flagged, left out)
 constexpr int MAX_BLOCK = 256;  // steps between checkpoints
 
 struct RefArgs {
@@ -337,14 +338,14 @@ __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, f
 // ---------------------------------------------------- classified-hit list
 struct Assigned {
     int n;
-    uint32_t key[CDC_MAX_FOUND];  // wire | partition << 16, sorted by wire
-    float drift[CDC_MAX_FOUND];
+    uint32_t key[MAX_ASSIGNED];  // wire | partition << 16, sorted by wire
+    float drift[MAX_ASSIGNED];
     // per pass: best closest approach in the assigned partition
-    float D[CDC_MAX_FOUND];
-    float nx[CDC_MAX_FOUND], ny[CDC_MAX_FOUND], nz[CDC_MAX_FOUND];
-    float u[CDC_MAX_FOUND];
-    int j[CDC_MAX_FOUND];         // segment start state; -1 start point, -2 end point
-    float J[CDC_MAX_FOUND][5];
+    float D[MAX_ASSIGNED];
+    float nx[MAX_ASSIGNED], ny[MAX_ASSIGNED], nz[MAX_ASSIGNED];
+    float u[MAX_ASSIGNED];
+    int j[MAX_ASSIGNED];          // segment start state; -1 start point, -2 end point
+    float J[MAX_ASSIGNED][5];
 
     __device__ __forceinline__ int find(int wire) const {
         int lo = 0, hi = n - 1;
@@ -712,7 +713,7 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     // entries with a minimum inside a segment, by segment descending (the
     // sweep's order) and by entry within a segment (insertion sort, stable):
     // the sweep takes them with a moving pointer instead of a scan of A per step
-    uint8_t ord[CDC_MAX_FOUND];
+    uint8_t ord[MAX_ASSIGNED];
     int n_ord = 0;
     for (int q = 0; q < A.n; ++q)
         if (A.j[q] >= 0) {
@@ -827,7 +828,10 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
         FoundList FL;
         T.init(G, P, s_lay, s_tab, dtab, &s_cand[0][threadIdx.x], 128, sf, FL);
         while (T.step(G, F, P, s_lay, s_tab, FL))
-            if (T.n % LIST_M == 0) T.rebuild(G, P, s_lay, s_tab);
+            if (T.n % LIST_M == 0) {
+                T.rebuild(G, P, s_lay, s_tab);
+                T.make_room(P, FL);
+            }
         flags |= T.flags;
         A.n = 0;
         for (int q = 0; q < T.nf; ++q) {  // each wire once, at its first entry
@@ -837,7 +841,11 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
             if (!first) continue;
             int part;
             record_class(FL.key, FL.r, T.nf, w, P.lam, part);
-            if (part >= 0) A.key[A.n++] = (uint32_t)w | ((uint32_t)part << 16);
+            if (part < 0) continue;
+            if (A.n < MAX_ASSIGNED)
+                A.key[A.n++] = (uint32_t)w | ((uint32_t)part << 16);
+            else
+                flags |= CDC_FLAG_FOUND_OVERFLOW;
         }
     }
     for (int q = 1; q < A.n; ++q) {  // sort by wire

@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                     my = -1;
                     break;
                 }
-                if ((it % LIST_M) == LIST_M - 1) T.rebuild(G, P, s_lay, s_tab);  // seeds start at chunk starts
+                if ((it % LIST_M) == LIST_M - 1) {  // seeds start at chunk starts
+                    T.rebuild(G, P, s_lay, s_tab);
+                    T.make_room(P, FL);
+                }
             }
         }
     }
@@ -604,6 +607,32 @@ __global__ void class_counts_kernel(int n_events, const int32_t* __restrict__ hi
         c = (c < 0 || c >= n_part) ? 0 : c + 1;
         atomicAdd(&counts[((size_t)e * np1 + t) * np1 + c], 1);
     }
+}
+
+// Eqs. 2-3 from the counts of n_sets events (one thread per partition j):
+// eff[j] = C_{j->j} / C_j, pur[j] = C_{j->j} / sum_{i >= 0} C_{i->j}, counts
+// summed over the events first (64-bit), NaN for a zero denominator.
+__global__ void efficiency_purity_kernel(int n_sets, const int32_t* __restrict__ counts, int n_part, float* eff,
+                                         float* pur) {
+    const int np1 = n_part + 1;
+    for (int k = threadIdx.x; k < n_part; k += blockDim.x) {
+        long long diag = 0, row = 0, col = 0;
+        for (int e = 0; e < n_sets; ++e) {
+            const int32_t* C = counts + (size_t)e * np1 * np1;
+            diag += C[(k + 1) * np1 + (k + 1)];
+            for (int j = 0; j <= n_part; ++j) row += C[(k + 1) * np1 + j];
+            for (int i = 1; i <= n_part; ++i) col += C[i * np1 + (k + 1)];
+        }
+        const float nan = __int_as_float(0x7fc00000);
+        eff[k] = row ? (float)((double)diag / (double)row) : nan;
+        pur[k] = col ? (float)((double)diag / (double)col) : nan;
+    }
+}
+
+cudaError_t launch_efficiency_purity(int n_sets, const int32_t* counts, int n_part, float* eff, float* pur,
+                                     cudaStream_t st) {
+    efficiency_purity_kernel<<<1, 32, 0, st>>>(n_sets, counts, n_part, eff, pur);
+    return cudaGetLastError();
 }
 
 // n_common[e] = hits of event e classified pa by one scan and pb by the other.

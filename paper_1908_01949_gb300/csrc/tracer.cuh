@@ -48,9 +48,10 @@ constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
 // Record of one seed: every distance minimum closer than drift + sqrt(lambda),
-// in track order (so partitions never decrease along it), as key = wire |
-// partition << 16 and r = D - drift (-inf where cheap bounds put D below
-// drift - sqrt(lambda)).
+// in track order (so the partitions of one wire never decrease along it), as
+// key = wire | partition << 16 and r = D - drift (-inf where cheap bounds put
+// D below drift - sqrt(lambda)); when it is nearly full it is compacted
+// (record_compact) before it overflows.
 struct FoundList {
     uint32_t key[CDC_MAX_FOUND];
     float r[CDC_MAX_FOUND];
@@ -107,6 +108,69 @@ __device__ __forceinline__ float record_score(const uint32_t* key, const float* 
         e += wire_term(key, r, n, i, w, lam, part) - lam;
     }
     return fmaf((float)H, lam, e);
+}
+
+// A full record made room for more minima without changing any term or
+// class: the entries of finished partitions (below cur) shrink to one per
+// wire, the nearest minimum of its best partition (ties to the lower one), and
+// vanish where that term is lambda; the current partition's entries of one
+// wire merge into the nearest.  Entries of a wire stay in partition order.
+// Returns the new number of entries.
+static __device__ __noinline__ int record_compact(uint32_t* key, float* r, int n, int cur, float lam) {
+    uint32_t keep[CDC_MAX_FOUND / 32];
+    for (int q = 0; q < CDC_MAX_FOUND / 32; ++q) keep[q] = 0u;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t k = key[i];
+        const int w = key_wire(k);
+        if (key_part(k) < cur) {
+            bool first = true;
+            for (int j = 0; j < i; ++j) first &= !(key_wire(key[j]) == w && key_part(key[j]) < cur);
+            if (!first) continue;
+            float best = lam, bm = 0.f, cm = r[i];
+            int bp = -1, cp = key_part(k);
+            for (int j = i + 1; j <= n; ++j) {
+                const bool same = j < n && key_wire(key[j]) == w && key_part(key[j]) < cur;
+                if (same && key_part(key[j]) == cp) {
+                    cm = fminf(cm, r[j]);
+                    continue;
+                }
+                if (j == n || same) {
+                    const float t = part_term(cm, lam);
+                    if (t < best) {
+                        best = t;
+                        bm = cm;
+                        bp = cp;
+                    }
+                    if (j < n) {
+                        cp = key_part(key[j]);
+                        cm = r[j];
+                    }
+                }
+            }
+            if (bp >= 0) {
+                key[i] = (uint32_t)w | ((uint32_t)bp << 16);
+                r[i] = bm;
+                keep[i >> 5] |= 1u << (i & 31);
+            }
+        } else {
+            bool first = true;
+            for (int j = 0; j < i; ++j) first &= key[j] != k;
+            if (!first) continue;
+            float cm = r[i];
+            for (int j = i + 1; j < n; ++j)
+                if (key[j] == k) cm = fminf(cm, r[j]);
+            r[i] = cm;
+            keep[i >> 5] |= 1u << (i & 31);
+        }
+    }
+    int m = 0;
+    for (int i = 0; i < n; ++i)
+        if (keep[i >> 5] & (1u << (i & 31))) {
+            key[m] = key[i];
+            r[m] = r[i];
+            ++m;
+        }
+    return m;
 }
 
 // Hit classification of `wire` from a record (sec. 2.2: d^2 < lambda): the
@@ -326,6 +390,12 @@ struct Tracer {
         } else {
             flags |= CDC_FLAG_FOUND_OVERFLOW;
         }
+    }
+
+    // Room in the record for the next LIST_M steps: compacted once it is
+    // nearly full (at most LIST_CAP minima per step are appended).
+    __device__ __forceinline__ void make_room(const ScanConst& P, FoundList& FL) {
+        if (nf > CDC_MAX_FOUND - LIST_M * LIST_CAP) nf = record_compact(FL.key, FL.r, nf, part, P.lam);
     }
 
     // Candidates for the next LIST_M segments at the current state:

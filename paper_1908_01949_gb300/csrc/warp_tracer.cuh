@@ -363,7 +363,16 @@ struct WarpTracer {
             advance(F, P);
             list_pass(G, P);
             if (!finish(G, P, s_lay, s_tab)) break;
-            if (n % LIST_M == 0) rebuild(G, P, s_lay, s_tab);
+            if (n % LIST_M == 0) {
+                rebuild(G, P, s_lay, s_tab);
+                if (nf > CDC_MAX_FOUND - LIST_M * LIST_CAP) {  // room for the next LIST_M steps, as Tracer::make_room
+                    __syncwarp();
+                    int m = 0;
+                    if (lane == 0) m = record_compact(rec->key, rec->r, nf, part, P.lam);
+                    nf = __shfl_sync(WARP_ALL, m, 0);
+                    __syncwarp();
+                }
+            }
         }
     }
 

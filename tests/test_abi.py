@@ -48,6 +48,20 @@ def test_binding_covers_every_entry_point():
             assert hasattr(_lib.Context, n)
 
 
+def test_every_entry_point_has_a_declared_signature():
+    """ctypes passes undeclared integer arguments as 32-bit ints, which would cut
+    64-bit device pointers: every exported call carries its argument types, and
+    as many as the header's declaration has parameters."""
+    from paper_1908_01949_gb300 import _lib
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    L = _lib.lib()
+    for n in _lib.EXPORTS:
+        decl = re.search(r"\b" + n + r"\s*\(([^)]*)\)", src).group(1)
+        n_params = 0 if decl.strip() in ("", "void") else decl.count(",") + 1
+        assert getattr(L, n).argtypes is not None, n
+        assert len(getattr(L, n).argtypes) == n_params, (n, len(getattr(L, n).argtypes), n_params)
+
+
 def test_struct_layouts_match_header():
     from paper_1908_01949_gb300 import _lib
     assert C.sizeof(_lib.cdc_grid) == 60

@@ -46,5 +46,24 @@ def test_scan_classification_efficiency_and_purity():
     torch.cuda.synchronize()
     hp = out["hit_part"].cpu().numpy()
     assert np.array_equal(counts.cpu().numpy(), O.classification_counts(off, hp, truth, 1))
-    eps, pur = cdc.efficiency_purity(counts.cpu().numpy())
+    eps, pur = (x.cpu().numpy() for x in tr.efficiency_purity(counts))
     assert eps[0] > 0.8 and pur[0] == 1.0
+
+
+def test_efficiency_and_purity_follow_the_oracle_formula():
+    """cdc_efficiency_purity (Eqs. 2-3 on the device, counts summed over the
+    events) against the oracle's formula on random counts, with empty rows and
+    columns giving NaN."""
+    import torch
+    rng = np.random.default_rng(1)
+    C = rng.integers(0, 9, (5, 4, 4)).astype(np.int32)
+    C[:, 2, :] = 0                                    # truth partition 1 absent: eps NaN
+    C[:, 1:, 3] = 0                                   # nothing classified 2: pur NaN
+    g, f = S.make_geometry(), S.uniform_field(1.0)
+    tr = tracker(g, f)
+    eps, pur = tr.efficiency_purity(torch.as_tensor(C, device=tr.dev))
+    torch.cuda.synchronize()
+    e0, p0 = O.efficiency_purity(C)
+    assert np.allclose(eps.cpu().numpy(), e0, rtol=1e-6, equal_nan=True)
+    assert np.allclose(pur.cpu().numpy(), p0, rtol=1e-6, equal_nan=True)
+    assert np.isnan(e0[1]) and np.isnan(p0[2])

@@ -28,11 +28,3 @@ def test_perfect_classification_and_event_sums():
     # labels beyond n_part count as -1
     C2 = O.classification_counts([0, 3], [5, 0, -7], [0, 0, 0], 1)
     assert C2[0].tolist() == [[0, 0], [2, 1]]
-
-
-def test_package_formula_matches_the_oracle():
-    import paper_1908_01949_gb300 as cdc
-    rng = np.random.default_rng(1)
-    C = rng.integers(0, 9, (5, 4, 4))
-    a, b = cdc.efficiency_purity(C), O.efficiency_purity(C)
-    assert np.allclose(a[0], b[0], equal_nan=True) and np.allclose(a[1], b[1], equal_nan=True)
