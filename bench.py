@@ -25,11 +25,13 @@ Legs (timed separately, reported beside the headline):
     batched Hough, and the FP32 steppers against the FP64 GPU stepper to 6 m;
   bidirectional, split_ab, event_loop: the ranked extensions.
 
---profile-case runs only the multi-turn leg on a 240000-seed coarse grid, and
---profile-batched N one eager call of the batched step on its first N events
-(fixed launch shape, no autotuning, so that the first scan-kernel launch is
-that call's coarse round), for profiler captures; their lines are marked as
-such and are not benchmark results.
+--profile-case runs only the multi-turn leg on a 240000-seed coarse grid
+(--profile-case full: on its 10^6-seed grid; with --profile-split also the
+two-kernel A/B leg on the same event), --profile-batched N one eager
+call of the batched step on its first N events (fixed launch shape, no
+autotuning, so that the first scan-kernel launch is that call's coarse round),
+and --profile-refine N only the refine leg on N events, for profiler captures;
+their lines are marked as such and are not benchmark results.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 a bounded sample of the headline workload instead.
@@ -67,13 +69,16 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # from one single-pass ncu capture of this benchmark's own launch; valid only for the kernel sources it was
 # taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
 TRAFFIC = {
-    "batched": {"bytes": None, "shape": None, "csrc_sha256": None},
-    "multi_turn": {"bytes": None, "shape": None, "csrc_sha256": None},
+    "batched": {"bytes": 2072439040 + 5973966080, "shape": "256x32",
+                "csrc_sha256": "7fc8990df8d701d5cc758258e646e5b739186cac33473202f81ea949bc78fcde"},
+    "multi_turn": {"bytes": 67645184 + 82392832, "shape": "256x32",
+                   "csrc_sha256": "7fc8990df8d701d5cc758258e646e5b739186cac33473202f81ea949bc78fcde"},
 }
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": None, "fma_pipe_active_pct": None, "csrc_sha256": None}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 277.4, "fma_pipe_active_pct": 40.3,
+               "csrc_sha256": "7fc8990df8d701d5cc758258e646e5b739186cac33473202f81ea949bc78fcde"}
 FFMA_ITERS = 4096                # iterations of the FP32 throughput kernel (~4 ms on a GB300)
 
 
@@ -548,7 +553,7 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
     n_in = max(1, int(args.inflight))
     evs = [S.cfg2_case(1000 * rank + k, fm, occupancy=0.10)[2] for k in range(n_in)]
     tmpl = S.cfg2_grid_template()
-    if args.profile_case:
+    if args.profile_case == "reduced":
         tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
     seeds_coarse = int(np.prod(tmpl["n"][0]))
     seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
@@ -1062,6 +1067,8 @@ def refine_leg(args, rank, local, g, fm, stream):
             "finite_start_seeds": int(ok_seed.sum().item()),
             "median_chi2_ratio": float(np.median(c1[ok] / c0[ok])) if ok.any() else None,
             "flagged": int((fl != 0).sum()),
+            "flagged_by_bit": {name.lower(): int(((fl & getattr(cdc, "FLAG_" + name)) != 0).sum())
+                               for name in ("STEP_CAP", "FOUND_OVERFLOW", "NOT_SPD", "DOCA_ZERO", "LOST_HIT", "BAD_HIT")},
             "seed_selection": f"64 best of one batched ten-round scan (k = 64) of {REFINE_SCAN_SEEDS} seeds per "
                               f"event around its first turn ({scan_s:.2f} s, not timed)",
             "timing": f"median of {args.refine_reps} CUDA-event timed calls"}
@@ -1103,20 +1110,37 @@ def run_cuda(args, ws, rank, local):
         if dist:
             dist.destroy_process_group()
         return
+    if args.profile_refine:
+        args.refine_events = args.profile_refine
+        rf = refine_leg(args, rank, local, g, fm, stream)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": rf["seeds_per_s"], "unit": "seeds/s", "n_gpus": ws,
+                              "steps": args.refine_reps, "warmup": args.warmup, "ms_per_step": rf["ms"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic",
+                              "config": {"workload": "refine leg", "profile_case":
+                                         f"the refine leg alone on {rf['events']} events for profiler captures, "
+                                         "not a benchmark result"},
+                              "refine": rf, "fp32_peak": peak}))
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.profile_case:
         mt = multi_turn_leg(args, ws, rank, local, g, fm, flush, peak)
+        ev0, grid0 = mt.pop("_cpu")
+        split = split_ab_leg(args, rank, local, g, fm, ev0, grid0, flush) if args.profile_split else None
         if rank == 0:
-            mt.pop("_cpu")
             print(json.dumps({"metric": METRIC, "value": mt["seeds_per_s"], "unit": "seeds/s", "n_gpus": ws,
                               "steps": args.mt_steps, "warmup": args.warmup, "ms_per_step": mt["ms_per_step"],
                               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                               "data": "synthetic",
                               "config": {"workload": WORKLOAD_MULTI_TURN, "profile_case":
-                                         "240000-seed coarse grid for profiler captures, not a benchmark result"},
+                                         ("240000-seed" if args.profile_case == "reduced" else "10^6-seed")
+                                         + " coarse grid for profiler captures, not a benchmark result"},
                               "coarse_scan": {"launch_ms": mt["roofline"]["launch_ms"],
                                               "rkn_steps": mt["roofline"]["rkn_steps"]},
                               "latency_ms_per_event": mt["latency_ms_per_event"], "multi_turn": mt,
-                              "fp32_peak": peak}))
+                              "split_ab": split, "fp32_peak": peak}))
         if dist:
             dist.destroy_process_group()
         return
@@ -1336,8 +1360,13 @@ def main():
                     help="distinct events in flight (one context and stream each) in the multi-turn leg")
     ap.add_argument("--profile-batched", type=int, default=0, metavar="N",
                     help="one eager call of the batched step on its first N events (profiler captures; not a result)")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="only the multi-turn leg on a 240000-seed coarse grid (profiler captures; not a result)")
+    ap.add_argument("--profile-refine", type=int, default=0, metavar="N",
+                    help="only the refine leg on N events (profiler captures; not a result)")
+    ap.add_argument("--profile-split", action="store_true",
+                    help="with --profile-case, also the two-kernel A/B leg on the same event (profiler captures)")
+    ap.add_argument("--profile-case", nargs="?", const="reduced", default=None, choices=["reduced", "full"],
+                    help="only the multi-turn leg on a 240000-seed coarse grid, or ('full') its 10^6-seed grid "
+                         "(profiler captures; not a result)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

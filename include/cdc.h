@@ -211,8 +211,11 @@ int cdc_scan_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int
  * surviving seeds in place of the Kalman fit of sec. 2.2).  Each seed first
  * classifies its event's hits as the scan does (d^2 < lambda -> partition);
  * then n_iter iterations minimise chi^2 = sum over classified hits of
- * ((DCA_k - drift)/sigma)^2 with J from forward tangents of the RKN step and
- * an FP64 Cholesky solve of the 5x5 normal equations in units of scale.
+ * ((DCA_k - drift)/sigma)^2 with J from forward tangents of the RKN step
+ * (theta0's column from the symmetry of the field about z) and an FP64
+ * Cholesky solve of the 5x5 normal equations in units of scale.  At most 256
+ * classified hits per seed enter chi^2 (more: CDC_FLAG_FOUND_OVERFLOW, the
+ * hits beyond the first 256 in the scan's record order are left out).
  * Device inputs: seed_event [n_seeds] (event of each seed, in [0, n_events);
  * a seed with another value gets CDC_FLAG_BAD_HIT and NaN outputs), seeds
  * [n_seeds][5], hit_off [n_events+1], wire_id, drift.  Device outputs: seeds_out

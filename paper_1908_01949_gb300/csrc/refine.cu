@@ -5,8 +5,9 @@
 // Per seed (one thread):
 //  1. classification of the event's hits at the starting seed, exactly as the
 //     scan does (d^2 < lambda -> partition), held fixed afterwards;
-//  2. Gauss-Newton iterations: an RKN pass that carries five forward tangent
-//     vectors d(r, t)/d(seed) through the linearised step, finds each
+//  2. Gauss-Newton iterations: an RKN pass that carries four forward tangent
+//     vectors d(r, t)/d(z0, px0, py0, pz0) through the linearised step (the
+//     theta0 column follows from the field's symmetry about z), finds each
 //     classified wire's closest approach in its partition, and forms
 //     residuals (DCA - drift)/sigma and J = n_hat . dP/dseed / sigma (envelope
 //     theorem); J^T J and J^T r are accumulated and the 5x5 system is solved
@@ -26,7 +27,7 @@
 namespace cdc {
 
 constexpr int MAX_CK = 64;      // checkpoints per seed
-constexpr int MAX_ASSIGNED = 128;  // classified hits refined per seed (more: flagged, left out)
+constexpr int MAX_ASSIGNED = 256;  // classified hits refined per seed; a three-turn signal has ~60-150 (more: flagged, left out)
 constexpr int MAX_BLOCK = 256;  // steps between checkpoints
 
 struct RefArgs {
@@ -224,14 +225,14 @@ __device__ __forceinline__ void rkn_step_stages(const DevField& F, State& s, flo
     acc2(s.tz, s.mz, tl[2], dl[2]);
 }
 
-// Tangent of one step: (dr, dt) of five directions, dlam constant.
-template <int KIND>
-__device__ __forceinline__ void tangent_step(const Stages<KIND>& S, float lam, float h, float (&dr)[5][3],
-                                             float (&dt)[5][3], const float (&dl)[5]) {
+// Tangent of one step: (dr, dt) of NT directions, dlam constant.
+template <int KIND, int NT>
+__device__ __forceinline__ void tangent_step(const Stages<KIND>& S, float lam, float h, float (&dr)[NT][3],
+                                             float (&dt)[NT][3], const float (&dl)[NT]) {
     const float h2 = 0.5f * h, hh8 = h * h * 0.125f, hh2 = h * h * 0.5f, hh6 = h * h * (1.0f / 6.0f),
                 h6 = h * (1.0f / 6.0f);
 #pragma unroll
-    for (int n = 0; n < 5; ++n) {
+    for (int n = 0; n < NT; ++n) {
         const float q = dl[n] / lam;
         float gv[3], c1[3], c2[3], d1[3], d2[3], d3[3], d4[3], ti[3], ri[3];
         apply_g<KIND>(S.g1, dr[n], gv);
@@ -495,6 +496,22 @@ __device__ __forceinline__ void hermite_w(float u, float h, float& a0, float& a1
     b1 = h * t2 * (t - 1.0f);                // h11 h: weight of t_{j+1}
 }
 
+// Row of the Jacobian (divided by sigma) of a distance whose unit normal is n
+// at track point P, from the tangents v of the seed's (z0, px0, py0, pz0).
+// The theta0 column needs no tangent of its own: the field is symmetric about
+// the z axis, so turning theta0 and the direction of (px0, py0) together by
+// an angle turns the whole track about z, with tangent z x P at every point;
+// turning (px0, py0) alone has tangent px0 v_py0 - py0 v_px0, and the theta0
+// tangent is the difference of the two.
+__device__ __forceinline__ void jac_row(const float nv[3], const float P[3], const float (&v)[4][3], float px0,
+                                        float py0, float sigma, float J[5]) {
+    const float w0 = fmaf(py0, v[1][0], fmaf(-px0, v[2][0], -P[1]));
+    const float w1 = fmaf(py0, v[1][1], fmaf(-px0, v[2][1], P[0]));
+    const float w2 = fmaf(py0, v[1][2], -px0 * v[2][2]);
+    J[0] = (nv[0] * w0 + nv[1] * w1 + nv[2] * w2) / sigma;
+    for (int m = 0; m < 4; ++m) J[1 + m] = (nv[0] * v[m][0] + nv[1] * v[m][1] + nv[2] * v[m][2]) / sigma;
+}
+
 // One propagation over the whole track that records, for every classified
 // wire, the closest approach inside its partition.  TAN: also the forward
 // tangents and J.  CK: also the checkpoints of the adjoint.
@@ -504,22 +521,20 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
                           float (*ck)[14], int ck_every, uint32_t& flags) {
     State s;
     seed_state_d(sd, G.R0d, P.charge_dir, P.direction, s);
-    float dr[5][3], dt[5][3], dl[5];
+    // tangents of (z0, px0, py0, pz0); theta0's follows from them (jac_row)
+    float dr[4][3], dt[4][3], dl[4];
+    const float px0 = (float)sd[2], py0 = (float)sd[3];
     if (TAN) {
         const double p = sqrt(sd[2] * sd[2] + sd[3] * sd[3] + sd[4] * sd[4]);
         const double dir = P.direction < 0 ? -1.0 : 1.0;
-        double st, ct;
-        sincos(sd[0], &st, &ct);
         const double th[3] = {sd[2] / p, sd[3] / p, sd[4] / p};
-        for (int n = 0; n < 5; ++n)
+        for (int n = 0; n < 4; ++n)
             for (int a = 0; a < 3; ++a) dr[n][a] = dt[n][a] = 0.f;
-        dr[0][0] = (float)(-G.R0d * st);
-        dr[0][1] = (float)(G.R0d * ct);
-        dr[1][2] = 1.0f;
-        dl[0] = dl[1] = 0.f;
+        dr[0][2] = 1.0f;
+        dl[0] = 0.f;
         for (int b = 0; b < 3; ++b) {
-            for (int a = 0; a < 3; ++a) dt[2 + b][a] = (float)(dir * (((a == b) ? 1.0 : 0.0) - th[a] * th[b]) / p);
-            dl[2 + b] = (float)(-(double)s.lam * th[b] / p);
+            for (int a = 0; a < 3; ++a) dt[1 + b][a] = (float)(dir * (((a == b) ? 1.0 : 0.0) - th[a] * th[b]) / p);
+            dl[1 + b] = (float)(-(double)s.lam * th[b] / p);
         }
     }
     for (int i = 0; i < A.n; ++i) {
@@ -547,9 +562,10 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
                 A.nx[q] = wp[0] * inv;
                 A.ny[q] = wp[1] * inv;
                 A.nz[q] = wp[2] * inv;
-                if (TAN)
-                    for (int m = 0; m < 5; ++m)
-                        A.J[q][m] = (A.nx[q] * dr[m][0] + A.ny[q] * dr[m][1] + A.nz[q] * dr[m][2]) / sigma;
+                if (TAN) {
+                    const float nv[3] = {A.nx[q], A.ny[q], A.nz[q]};
+                    jac_row(nv, o, dr, px0, py0, sigma, A.J[q]);
+                }
             }
         });
     }
@@ -561,16 +577,16 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
             c[13] = s.lam_lo;
         }
         const float o[6] = {s.rx, s.ry, s.rz, s.tx, s.ty, s.tz}, ol[3] = {s.lx, s.ly, s.lz};
-        float odr[5][3], odt[5][3];
+        float odr[4][3], odt[4][3];
         if (TAN) {
-            for (int m = 0; m < 5; ++m)
+            for (int m = 0; m < 4; ++m)
                 for (int a = 0; a < 3; ++a) {
                     odr[m][a] = dr[m][a];
                     odt[m][a] = dt[m][a];
                 }
             Stages<KIND> S;
             rkn_step_stages<KIND>(F, s, h, P.h6_lo, S);
-            tangent_step<KIND>(S, s.lam, h, dr, dt, dl);
+            tangent_step<KIND, 4>(S, s.lam, h, dr, dt, dl);
         } else {
             rkn_step<KIND, true>(F, s, h, P.h6_lo);
         }
@@ -594,12 +610,13 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
             if (TAN) {
                 float a0, a1, b0, b1;
                 hermite_w(u, h, a0, a1, b0, b1);
-                for (int m = 0; m < 5; ++m) {
-                    float v[3];
+                float v[4][3], Pu[3];
+                for (int m = 0; m < 4; ++m)
                     for (int a = 0; a < 3; ++a)
-                        v[a] = fmaf(a0, odr[m][a], fmaf(a1, odt[m][a], fmaf(b0, dr[m][a], b1 * dt[m][a])));
-                    A.J[q][m] = (A.nx[q] * v[0] + A.ny[q] * v[1] + A.nz[q] * v[2]) / sigma;
-                }
+                        v[m][a] = fmaf(a0, odr[m][a], fmaf(a1, odt[m][a], fmaf(b0, dr[m][a], b1 * dt[m][a])));
+                for (int a = 0; a < 3; ++a)
+                    Pu[a] = fmaf(a0, o[a], fmaf(a1, o[3 + a], fmaf(b0, nn[a], b1 * nn[3 + a])));
+                jac_row(wp, Pu, v, px0, py0, sigma, A.J[q]);
             }
         });
         const bool now_out = rho >= G.R0;
@@ -632,9 +649,10 @@ __device__ int track_pass(const DevGeom& G, const DevField& F, const ScanConst& 
                         A.nx[q] = wp[0] * inv;
                         A.ny[q] = wp[1] * inv;
                         A.nz[q] = wp[2] * inv;
-                        if (TAN)
-                            for (int m = 0; m < 5; ++m)
-                                A.J[q][m] = (A.nx[q] * dr[m][0] + A.ny[q] * dr[m][1] + A.nz[q] * dr[m][2]) / sigma;
+                        if (TAN) {
+                            const float nv[3] = {A.nx[q], A.ny[q], A.nz[q]};
+                            jac_row(nv, nn, dr, px0, py0, sigma, A.J[q]);
+                        }
                     }
                 });
             break;
@@ -713,6 +731,7 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     // entries with a minimum inside a segment, by segment descending (the
     // sweep's order) and by entry within a segment (insertion sort, stable):
     // the sweep takes them with a moving pointer instead of a scan of A per step
+    static_assert(MAX_ASSIGNED <= 256, "entry indices are kept in 8 bits");
     uint8_t ord[MAX_ASSIGNED];
     int n_ord = 0;
     for (int q = 0; q < A.n; ++q)
