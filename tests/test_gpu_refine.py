@@ -161,3 +161,40 @@ def test_empty_call_and_a_seed_whose_event_has_no_hits():
     assert int(both["n_used"][1]) > 0 and float(both["chi2"][1]) > 0.0
     for k in ("seeds", "chi2", "grad", "n_used", "flags"):
         assert torch.equal(both[k][1:], alone[k]), k
+
+
+def test_three_turn_seed_with_more_than_128_classified_hits(field_map):
+    """A three-turn signal classifies up to ~150 hits (the refine workload's
+    events); every one of them enters chi^2: n_used, chi^2 and the adjoint
+    gradient at seeds near the truth follow the oracle, with no overflow flag."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    ev = S.cfg4_event(1, field_map)[0]
+    tr = tracker(g, field_map)
+    off, wid, dr = tr.events_to_device([0, ev.wire_id.size], ev.wire_id, ev.drift)
+    sp = cdc.scan_params(h=2.0, max_steps=3500, lam=4.0, max_partitions=3)
+    rp = cdc.refine_params(n_iter=0, sigma=0.2, checkpoint=128)
+    rng = np.random.default_rng(5)
+    sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * 0.1
+    seeds = np.asarray([ev.truth_seeds[0] + rng.normal(0, 1, 5) * sig for _ in range(4)], np.float32)
+    se = torch.zeros(len(seeds), dtype=torch.int32, device=tr.dev)
+    out = tr.chi2_grad(se, torch.as_tensor(seeds, device=tr.dev), off, wid, dr, sp, rp)
+    torch.cuda.synchronize()
+    c2, gr = out["chi2"].cpu().numpy(), out["grad"].cpu().numpy()
+    nu, fl = out["n_used"].cpu().numpy(), out["flags"].cpu().numpy()
+    op = oracle_params(sp)
+    checked = 0
+    for i, sd in enumerate(seeds.astype(np.float64)):
+        part, margin = _oracle_part(g, field_map, ev, sd, op)
+        if (margin < 1e-3).any():
+            continue
+        rc2, rg, _, rnu, _ = O.chi2(g, field_map, op, ev.wire_id, ev.drift.astype(np.float64), part, sd)
+        assert rnu > 128, rnu                 # the case this test is about
+        assert not (fl[i] & cdc.FLAG_FOUND_OVERFLOW)
+        assert nu[i] == rnu
+        assert abs(c2[i] - rc2) <= 1e-4 * rc2, (i, c2[i], rc2)
+        rel = np.linalg.norm((gr[i] - rg) * SCALE) / np.linalg.norm(rg * SCALE)
+        assert rel <= 1e-4, (i, rel, gr[i], rg)
+        checked += 1
+    assert checked >= 2
