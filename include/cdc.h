@@ -281,10 +281,11 @@ int cdc_fp32_peak(cdc_ctx* ctx, int iters, double* tflops, double* ms, void* str
  * block of the one-lane-per-seed kernel (128 or 256); chunk = RKN steps a lane
  * takes between seed refills (16 or 32); warp_seeds = zoom rounds with at most
  * this many seeds (n_events * n_zoom * 243) run one warp per seed instead,
- * which shortens rounds too small to fill the GPU (0: never).  Every shape
- * keeps 768 resident threads per SM; the results do not depend on block and
- * chunk, and the warp kernel records the same minima in the same order.  A
- * new context uses {256, 16, 16 * number of SMs}. */
+ * which shortens rounds too small to fill the GPU (0: never).  128-thread
+ * blocks keep 896 resident threads per SM, 256-thread blocks 768; the results
+ * do not depend on block and chunk, and the warp kernel records the same
+ * minima in the same order.  A new context uses {128, 32, 16 * number of
+ * SMs}. */
 typedef struct {
     int32_t block;
     int32_t chunk;

@@ -46,7 +46,7 @@ struct cdc_ctx {
     int8_t* split_end = nullptr;
     int split_chunk = 0, split_steps = 0;
     // scan-kernel launch shape (cdc_scan_config)
-    int scan_block = 256, scan_chunk = 16, scan_warp_seeds = 0;
+    int scan_block = 128, scan_chunk = 32, scan_warp_seeds = 0;
     // kernel timer
     bool timer_on = false, timer_keep = false;
     std::vector<cudaEvent_t> timer_ev;
@@ -315,17 +315,24 @@ int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float*
     if (!bz || !br) return fail(c, CDC_ERR_ARG, "field map array is NULL");
     if (nr < 2 || nz < 2 || (long long)nr * nz > (1ll << 28)) return fail(c, CDC_ERR_RANGE, "map size");
     if (!(dr > 0.f) || !(dz > 0.f) || !(r_min >= 0.f)) return fail(c, CDC_ERR_ARG, "need dr, dz > 0 and r_min >= 0");
-    const size_t ncell = (size_t)(nr - 1) * (nz - 1);
+    // Cell (ip, jp) of the (nr + 1) x (nz + 1) table covers the map cell (ip - 1, jp - 1); the border
+    // rows and columns hold the edge values with no dependence on the clamped coordinate, so a
+    // position beyond the grid, whose cell index is clamped into the border, reads the field at the
+    // nearest edge point (the map's clamped interpolation) without clamping its coordinates.
+    const size_t ncell = (size_t)(nr + 1) * (nz + 1);
     std::vector<float4> cells(2 * ncell);
     double bmax = 0.0;  // |B| of the bilinear field never exceeds the largest sample norm
     for (size_t q = 0; q < (size_t)nr * nz; ++q) bmax = std::max(bmax, hypot((double)bz[q], (double)br[q]));
-    for (int i = 0; i + 1 < nr; ++i)
-        for (int j = 0; j + 1 < nz; ++j) {
+    for (int ip = 0; ip <= nr; ++ip)
+        for (int jp = 0; jp <= nz; ++jp) {
+            // the map cell's corner indices, each clamped into the grid; a border cell repeats its edge
+            const int i0 = std::min(std::max(ip - 1, 0), nr - 1), i1 = std::min(ip, nr - 1);
+            const int j0 = std::min(std::max(jp - 1, 0), nz - 1), j1 = std::min(jp, nz - 1);
             const float* m[2] = {bz, br};
             for (int q = 0; q < 2; ++q) {
-                double v00 = m[q][(size_t)i * nz + j], v10 = m[q][(size_t)(i + 1) * nz + j];
-                double v01 = m[q][(size_t)i * nz + j + 1], v11 = m[q][(size_t)(i + 1) * nz + j + 1];
-                cells[2 * ((size_t)i * (nz - 1) + j) + q] =
+                double v00 = m[q][(size_t)i0 * nz + j0], v10 = m[q][(size_t)i1 * nz + j0];
+                double v01 = m[q][(size_t)i0 * nz + j1], v11 = m[q][(size_t)i1 * nz + j1];
+                cells[2 * ((size_t)ip * (nz + 1) + jp) + q] =
                     make_float4((float)v00, (float)(v10 - v00), (float)(v01 - v00), (float)(v11 - v10 - v01 + v00));
             }
         }
@@ -344,6 +351,8 @@ int cdc_load_field(cdc_ctx* c, int kind, float b0, const float* bz, const float*
     F.z_min = z_min;
     F.inv_dr = 1.0f / dr;
     F.inv_dz = 1.0f / dz;
+    F.u_off = 1.0f - r_min * F.inv_dr;  // padded cell coordinates: (rho - r_min) / dr + 1
+    F.v_off = 1.0f - z_min * F.inv_dz;
     F.r_max = r_min + dr * (float)(nr - 1);
     F.z_max = z_min + dz * (float)(nz - 1);
     F.dr = dr;

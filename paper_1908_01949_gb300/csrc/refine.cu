@@ -93,7 +93,7 @@ __device__ __forceinline__ void field_grad(const DevField& F, const float r[3], 
     const int i = min((int)u, F.nr - 2), j = min((int)v, F.nz - 2);
     u -= (float)i;
     v -= (float)j;
-    const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
+    const float4* c = F.cells + 2 * ((i + 1) * (F.nz + 1) + (j + 1));  // interior cell of the padded table
     float4 qz, qr;
     load_cell(c, qz, qr);
     const float bz = fmaf(v, fmaf(qz.w, u, qz.z), fmaf(qz.y, u, qz.x));
@@ -267,10 +267,14 @@ __device__ __forceinline__ void tangent_step(const Stages<KIND>& S, float lam, f
 }
 
 // Transposed step: given (rb, tb) at the step's end, returns them at its start
-// and adds to lb (d/d lam).
+// and adds to lb (d/d lam).  The step's increments are formed in FP32 and
+// added to the adjoint as compensated sums ((rb, rl), (tb, tl), (lb, ll)):
+// over a three-turn track the adjoint takes thousands of small increments, and
+// plain FP32 sums would leave an error of ~1e-4 of the gradient near the chi^2
+// minimum, where it is a small difference of much larger per-hit terms.
 template <int KIND>
 __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, float h, float rb[3], float tb[3],
-                                             float& lb) {
+                                             float& lb, float rl[3], float tl[3], float& ll) {
     const float h2 = 0.5f * h, hh8 = h * h * 0.125f, hh2 = h * h * 0.5f, hh6 = h * h * (1.0f / 6.0f),
                 h6 = h * (1.0f / 6.0f);
     float kb1[3], kb2[3], kb3[3], kb4[3], rn[3], tn[3], tbi[3], Bb[3], rbe[3], c[3];
@@ -279,15 +283,15 @@ __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, f
         kb2[a] = fmaf(hh6, rb[a], 2.0f * h6 * tb[a]);
         kb3[a] = kb2[a];
         kb4[a] = h6 * tb[a];
-        rn[a] = rb[a];                    // r' = r + ...
-        tn[a] = fmaf(h, rb[a], tb[a]);    // r' depends on h t; t' on t
+        rn[a] = 0.f;                      // increments: r' = r + ...
+        tn[a] = h * rb[a];                // r' depends on h t; t' on t
     }
     // k4 = lam t4 x B4 at re
     cross3(S.B4, kb4, c);
     for (int a = 0; a < 3; ++a) tbi[a] = lam * c[a];
     cross3(kb4, S.t4, c);
     for (int a = 0; a < 3; ++a) Bb[a] = lam * c[a];
-    lb += kb4[0] * S.k4[0] / lam + kb4[1] * S.k4[1] / lam + kb4[2] * S.k4[2] / lam;
+    float dl = kb4[0] * S.k4[0] / lam + kb4[1] * S.k4[1] / lam + kb4[2] * S.k4[2] / lam;
     rbe[0] = rbe[1] = rbe[2] = 0.f;
     apply_gt<KIND>(S.g4, Bb, rbe);
     for (int a = 0; a < 3; ++a) {
@@ -303,7 +307,7 @@ __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, f
     for (int a = 0; a < 3; ++a) tbi[a] = lam * c[a];
     cross3(kb3, S.t3, c);
     for (int a = 0; a < 3; ++a) Bb2[a] = lam * c[a];
-    lb += (kb3[0] * S.k3[0] + kb3[1] * S.k3[1] + kb3[2] * S.k3[2]) / lam;
+    dl += (kb3[0] * S.k3[0] + kb3[1] * S.k3[1] + kb3[2] * S.k3[2]) / lam;
     for (int a = 0; a < 3; ++a) {
         tn[a] += tbi[a];                                  // t3 = t + h/2 k2
         kb2[a] = fmaf(h2, tbi[a], kb2[a]);
@@ -313,7 +317,7 @@ __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, f
     for (int a = 0; a < 3; ++a) tbi[a] = lam * c[a];
     cross3(kb2, S.t2, c);
     for (int a = 0; a < 3; ++a) Bb2[a] = fmaf(lam, c[a], Bb2[a]);
-    lb += (kb2[0] * S.k2[0] + kb2[1] * S.k2[1] + kb2[2] * S.k2[2]) / lam;
+    dl += (kb2[0] * S.k2[0] + kb2[1] * S.k2[1] + kb2[2] * S.k2[2]) / lam;
     float rbm[3] = {0.f, 0.f, 0.f};
     apply_gt<KIND>(S.g2, Bb2, rbm);
     for (int a = 0; a < 3; ++a) {
@@ -328,12 +332,13 @@ __device__ __forceinline__ void adjoint_step(const Stages<KIND>& S, float lam, f
     for (int a = 0; a < 3; ++a) tn[a] = fmaf(lam, c[a], tn[a]);
     cross3(kb1, S.t1, c);
     for (int a = 0; a < 3; ++a) Bb[a] = lam * c[a];
-    lb += (kb1[0] * S.k1[0] + kb1[1] * S.k1[1] + kb1[2] * S.k1[2]) / lam;
+    dl += (kb1[0] * S.k1[0] + kb1[1] * S.k1[1] + kb1[2] * S.k1[2]) / lam;
     apply_gt<KIND>(S.g1, Bb, rn);
     for (int a = 0; a < 3; ++a) {
-        rb[a] = rn[a];
-        tb[a] = tn[a];
+        kahan(rb[a], rl[a], rn[a]);
+        kahan(tb[a], tl[a], tn[a]);
     }
+    kahan(lb, ll, dl);
 }
 
 // ---------------------------------------------------- classified-hit list
@@ -720,13 +725,14 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     if (!grad) return chi2;
     // backward sweep over blocks of steps
     float rb[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f}, lb = 0.f;
+    float rl[3] = {0.f, 0.f, 0.f}, tl[3] = {0.f, 0.f, 0.f}, ll = 0.f;  // low words of the compensated sums
     const float h = P.h;
     // end point minima inject into the last state
     for (int q = 0; q < A.n; ++q)
         if (A.j[q] == -2) {
-            rb[0] += A.D[q] * A.nx[q];
-            rb[1] += A.D[q] * A.ny[q];
-            rb[2] += A.D[q] * A.nz[q];
+            kahan(rb[0], rl[0], A.D[q] * A.nx[q]);
+            kahan(rb[1], rl[1], A.D[q] * A.ny[q]);
+            kahan(rb[2], rl[2], A.D[q] * A.nz[q]);
         }
     // entries with a minimum inside a segment, by segment descending (the
     // sweep's order) and by entry within a segment (insertion sort, stable):
@@ -769,8 +775,8 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
                 hermite_w(A.u[q], h, a0, a1, b0, b1);
                 const float nv[3] = {A.D[q] * A.nx[q], A.D[q] * A.ny[q], A.D[q] * A.nz[q]};
                 for (int a = 0; a < 3; ++a) {
-                    rb[a] = fmaf(b0, nv[a], rb[a]);
-                    tb[a] = fmaf(b1, nv[a], tb[a]);
+                    kahan(rb[a], rl[a], b0 * nv[a]);
+                    kahan(tb[a], tl[a], b1 * nv[a]);
                     pr[a] = fmaf(a0, nv[a], pr[a]);
                     ptt[a] = fmaf(a1, nv[a], ptt[a]);
                 }
@@ -779,19 +785,25 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
             const float r[3] = {buf[j - j0][0], buf[j - j0][1], buf[j - j0][2]};
             const float t[3] = {buf[j - j0][3], buf[j - j0][4], buf[j - j0][5]};
             S.eval(F, r, t, lam, h);
-            adjoint_step<KIND>(S, lam, h, rb, tb, lb);
+            adjoint_step<KIND>(S, lam, h, rb, tb, lb, rl, tl, ll);
             for (int a = 0; a < 3; ++a) {
-                rb[a] += pr[a];
-                tb[a] += ptt[a];
+                kahan(rb[a], rl[a], pr[a]);
+                kahan(tb[a], tl[a], ptt[a]);
             }
         }
     }
     for (int q = 0; q < A.n; ++q)
         if (A.j[q] == -1) {
-            rb[0] += A.D[q] * A.nx[q];
-            rb[1] += A.D[q] * A.ny[q];
-            rb[2] += A.D[q] * A.nz[q];
+            kahan(rb[0], rl[0], A.D[q] * A.nx[q]);
+            kahan(rb[1], rl[1], A.D[q] * A.ny[q]);
+            kahan(rb[2], rl[2], A.D[q] * A.nz[q]);
         }
+    double rbd[3], tbd[3];
+    for (int a = 0; a < 3; ++a) {
+        rbd[a] = (double)rb[a] + (double)rl[a];
+        tbd[a] = (double)tb[a] + (double)tl[a];
+    }
+    const double lbd = (double)lb + (double)ll;
     // seed: r0 = (R0 cos th, R0 sin th, z0), t0 = dir p/|p|, lam = q' kappa/|p|
     const double p = sqrt(sd[2] * sd[2] + sd[3] * sd[3] + sd[4] * sd[4]);
     const double dir = P.direction < 0 ? -1.0 : 1.0;
@@ -799,10 +811,10 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     double st, ct;
     sincos(sd[0], &st, &ct);
     const double th[3] = {sd[2] / p, sd[3] / p, sd[4] / p};
-    const double tdot = th[0] * tb[0] + th[1] * tb[1] + th[2] * tb[2];
-    grad[0] = (float)(-G.R0d * st * rb[0] + G.R0d * ct * rb[1]);
-    grad[1] = rb[2];
-    for (int b = 0; b < 3; ++b) grad[2 + b] = (float)(dir * (tb[b] - th[b] * tdot) / p - (double)lb * lam0 * th[b] / p);
+    const double tdot = th[0] * tbd[0] + th[1] * tbd[1] + th[2] * tbd[2];
+    grad[0] = (float)(-G.R0d * st * rbd[0] + G.R0d * ct * rbd[1]);
+    grad[1] = (float)rbd[2];
+    for (int b = 0; b < 3; ++b) grad[2 + b] = (float)(dir * (tbd[b] - th[b] * tdot) / p - lbd * lam0 * th[b] / p);
     return chi2;
 }
 
@@ -814,7 +826,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, ScanConst P, RefArgs a, int do_gn) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
-    __shared__ float4 s_cand[LIST_CAP][128];
+    __shared__ ListEntry s_cand[LIST_CAP][128];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
@@ -845,7 +857,7 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
     {
         Tracer<KIND> T;
         FoundList FL;
-        T.init(G, P, s_lay, s_tab, dtab, &s_cand[0][threadIdx.x], 128, sf, FL);
+        T.init(G, F, P, s_lay, s_tab, dtab, &s_cand[0][threadIdx.x], 128, sf, FL);
         while (T.step(G, F, P, s_lay, s_tab, FL))
             if (T.n % LIST_M == 0) {
                 T.rebuild(G, P, s_lay, s_tab);

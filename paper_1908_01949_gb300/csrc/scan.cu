@@ -222,14 +222,16 @@ __global__ void __launch_bounds__(1024) order_blocks_kernel(int n_events, const 
 // on short tracks.  Scores are written at the seeds' row-major indices; in
 // zoom rounds a seed that reaches its event's best score so far also keeps
 // its record of scored wires (record_slot).
-// BS threads per block, 768 resident threads per SM for every shape (the
-// register budget stays 80 per thread).
+// BS threads per block: seven 128-thread blocks per SM (28 warps, 72 registers
+// per thread) or three 256-thread blocks (24 warps, 80 registers); the
+// shorter register budget costs a few spilled words outside the stepping loop
+// and its extra warps hide more of the field-load latency.
 template <int KIND, int BS, int CHUNK>
-__global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
+__global__ void __launch_bounds__(BS, 896 / BS) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
     static_assert(CHUNK % LIST_M == 0, "candidate lists restart at chunk boundaries");
-    __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
+    extern __shared__ DevLayer s_lay[];  // [G.n_layers]: dynamic, so three blocks' lists and tables leave 192 KB of L1
     __shared__ uchar2 s_tab[TAB_N];
-    __shared__ float4 s_cand[LIST_CAP][BS];
+    __shared__ ListEntry s_cand[LIST_CAP][BS];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(BS, 768 / BS) scan_kernel(DevGeom G, DevField 
                     float sd[5];
                     my = io.seed_off[ev] + event_seed_ordered(io.grids, io.gpe, ev, s - io.seed_off[ev], sd,
                                                               io.perm ? io.perm + (size_t)ev * PERM_CAP : nullptr);
-                    T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires),
+                    T.init(G, F, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires),
                            &s_cand[0][threadIdx.x], BS, sd, FL);
                 } else {
                     my = -2;
@@ -486,7 +488,8 @@ __global__ void __launch_bounds__(128) scan_warp_kernel(DevGeom G, DevField F, S
         const int ev = find_event(io.seed_off, io.n_events, (long long)s);
         float sd[5];
         event_seed(io.grids, io.gpe, ev, (long long)s - io.seed_off[ev], sd);
-        T.init(G, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_rec[threadIdx.x >> 5], sd);
+        T.init(G, F, P, s_lay, s_tab, io.drift_tab + (size_t)ev * event_stride(G.n_wires), &s_rec[threadIdx.x >> 5],
+               sd);
         T.run(G, F, P, s_lay, s_tab);
         const float score = T.score(P, io.hit_off[ev + 1] - io.hit_off[ev]);
         if (lane == 0) {
@@ -582,7 +585,7 @@ __global__ void __launch_bounds__(128) assign_kernel(DevGeom G, DevField F, Scan
     }
     WarpFound* rec = &s_rec[threadIdx.x >> 5];
     WarpTracer<KIND> T;
-    T.init(G, P, s_lay, s_tab, drift_tab + (size_t)e * event_stride(G.n_wires), rec, sd);
+    T.init(G, F, P, s_lay, s_tab, drift_tab + (size_t)e * event_stride(G.n_wires), rec, sd);
     T.run(G, F, P, s_lay, s_tab);
     for (int h = h0 + lane; h < h1; h += 32) {
         const int w = wire_id[h];
@@ -748,9 +751,14 @@ __global__ void propagate_kernel(DevGeom G, DevField F, ScanConst P, int n_seeds
         for (int a = 0; a < 3; ++a) pos[((size_t)i * n_rec + r) * 3 + a] = nan;
     int n = 0, part = 0;
     bool outside = true;
+    float bx, by, bz;  // the scan stepper's field of the last end estimate
+    field_eval<KIND>(F, s.rx, s.ry, s.rz, bx, by, bz);
     for (;;) {
         if (n >= P.max_steps) break;
-        rkn_step<KIND, LAM2>(F, s, P.h, P.h6_lo);
+        if (LAM2)
+            rkn_step<KIND, true>(F, s, P.h, P.h6_lo);
+        else
+            rkn_step_fsal<KIND>(F, s, bx, by, bz, P.h, P.h6_lo);
         ++n;
         if (n % every == 0 && n / every <= n_rec) {
             double* o = pos + ((size_t)i * n_rec + (n / every - 1)) * 3;
@@ -789,7 +797,7 @@ __device__ void field_eval_d(const DevField& F, double x, double y, double z, do
     int i = min((int)u, F.nr - 2), j = min((int)v, F.nz - 2);
     u -= i;
     v -= j;
-    const float4* c = F.cells + 2 * (i * (F.nz - 1) + j);
+    const float4* c = F.cells + 2 * ((i + 1) * (F.nz + 1) + (j + 1));  // interior cell of the padded table
     float4 cz = c[0], cr = c[1];
     bz = (double)cz.x + (double)cz.y * u + (double)cz.z * v + (double)cz.w * u * v;
     double br = (double)cr.x + (double)cr.y * u + (double)cr.z * v + (double)cr.w * u * v;
@@ -907,8 +915,9 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
         return err;
     const int bs = L.block == 128 ? 128 : 256;
     const ScanKernel kern = F.kind == 0 ? scan_kernel_of<0>(bs, L.chunk) : scan_kernel_of<1>(bs, L.chunk);
+    const size_t lay_smem = sizeof(DevLayer) * (size_t)G.n_layers;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, lay_smem);
     const int scan_blocks = num_sms * (occ > 0 ? occ : 1);
     if (W.rec_count && L.n_rounds > 1 && (L.hit_part || L.hit_res2) &&
         (err = cudaMemsetAsync(W.rec_count, 0, sizeof(unsigned) * ne, st)) != cudaSuccess)
@@ -957,7 +966,7 @@ cudaError_t launch_scan(const DevGeom& G, const DevField& F, const ScanConst& P,
             // blocks would only contend for SM slots with other streams' work
             const int nb = r == 0 ? scan_blocks
                                   : (int)std::min<long long>(scan_blocks, std::max<long long>(1, (round_seeds + 31) / 32));
-            kern<<<nb, bs, 0, st>>>(G, F, P, io);
+            kern<<<nb, bs, lay_smem, st>>>(G, F, P, io);
         }
         if (timed) {
             timer_mark(L.timer.ev[*L.timer.used + 1], st);

@@ -54,8 +54,10 @@ __global__ void __launch_bounds__(128) record_kernel(DevGeom G, DevField F, Scan
     bool outside = true, stop = false;
     rr[0] = make_float4(st.rx, st.ry, st.rz, __int_as_float(0));
     rt[0] = make_float4(st.tx, st.ty, st.tz, 0.f);
+    float bx, by, bz;  // field of the last end estimate (the scan's stepper)
+    field_eval<KIND>(F, st.rx, st.ry, st.rz, bx, by, bz);
     while (!stop) {
-        rkn_step<KIND>(F, st, P.h, P.h6_lo);
+        rkn_step_fsal<KIND>(F, st, bx, by, bz, P.h, P.h6_lo);
         ++k;
         const float rho = rho_of(st.rx, st.ry);
         const bool now_out = rho >= G.R0;

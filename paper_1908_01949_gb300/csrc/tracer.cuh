@@ -47,6 +47,15 @@ namespace cdc {
 constexpr int LIST_CAP = 8;            // candidate wires per seed
 constexpr float PARALLEL_T2 = 0.25f;   // |t_perp|^2 below which receding wires are kept
 
+// One wire of a per-seed candidate list: wire | layer << 16 and the slope g
+// of the squared distance at the last state (the drift is read again from the
+// event table when a minimum is found; 8 bytes per entry keep the lists small
+// beside the L1 cache that holds the field map).
+struct __align__(8) ListEntry {
+    uint32_t key;
+    float g;
+};
+
 // Record of one seed: every distance minimum closer than drift + sqrt(lambda),
 // in track order (so the partitions of one wire never decrease along it), as
 // key = wire | partition << 16 and r = D - drift (-inf where cheap bounds put
@@ -210,7 +219,7 @@ __device__ __forceinline__ bool layer_cells(const DevLayer& L, const uint32_t* f
 }
 
 // Visits the fired wires in the search window around (rho, phi, z), layer by
-// layer and cell by cell: fn(wire, drift, cosa).  Only fired wires touch the
+// layer and cell by cell: fn(wire, drift, cosa, layer).  Only fired wires touch the
 // drift table.  The per-layer arithmetic is that of layer_cells, written out
 // here: the stepping loop's register allocation is better that way.
 template <class Fn>
@@ -247,7 +256,7 @@ __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2
             if (ii >= L.N) ii -= L.N;
             const int wire = L.base + ii;
             const float d = __ldg(dtab + wire);
-            if (d <= max_drift) fn(wire, d, L.cosa);
+            if (d <= max_drift) fn(wire, d, L.cosa, l);
         }
     }
 }
@@ -369,10 +378,11 @@ __device__ __forceinline__ float seg_res(const ScanConst& P, float kap, float ox
 template <int KIND>
 struct Tracer {
     State s;
+    float bx, by, bz;                 // field at the last step's end estimate (at the seed before the first)
     float ox, oy, oz, otx, oty, otz;  // state before the last step (high words)
     const float* dtab;
     const uint32_t* fired;
-    float4* cand;   // this thread's list column: cand[k * stride] = (wire bits, g, drift, cosa)
+    ListEntry* cand;  // this thread's list column: cand[k * stride]
     int stride;
     int n, part, nf, nc;
     bool outside, over;
@@ -430,7 +440,7 @@ struct Tracer {
         const float rlo = fmaxf(fmaxf(sqrtf(fmaxf(qlo, 0.f)) - 0.01f, rho - wide), 0.f);
         const float rhi = fminf(sqrtf(qhi) + 0.01f, rho + wide);
         visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win + wide, rho, atan2f(y, x), z,
-                     [&](int wire, float d, float cosa) {
+                     [&](int wire, float d, float cosa, int layer) {
                          const float4 W = __ldg(G.wires + wire);
                          float tp2;
                          const float g = dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2);
@@ -444,7 +454,7 @@ struct Tracer {
                              keep = fmaf(reach, fmaf(kap, fmaf(1.5f, reach, sqrt_ub(wp2)), tp2), g) + 1e-3f >= 0.f &&
                                     fmaf(wp2, tp2, -g * g) <= lim * lim * tp2;
                          }
-                         if (keep && !sink(wire, g, d, cosa)) over = true;
+                         if (keep && !sink(wire, g, layer)) over = true;
                      },
                      rlo, rhi);
     }
@@ -453,19 +463,20 @@ struct Tracer {
     __device__ __forceinline__ void rebuild(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
                                             const uchar2* s_tab) {
         nc = 0;
-        collect(G, P, s_lay, s_tab, [&](int wire, float g, float d, float cosa) {
+        collect(G, P, s_lay, s_tab, [&](int wire, float g, int layer) {
             if (nc >= LIST_CAP) return false;
-            cand[nc * stride] = make_float4(__int_as_float(wire), g, d, cosa);
+            cand[nc * stride] = ListEntry{(uint32_t)wire | ((uint32_t)layer << 16), g};
             ++nc;
             return true;
         });
     }
 
     // Seed state, the start-of-track minima and the first candidate list.
-    __device__ __forceinline__ void init(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
-                                         const uchar2* s_tab, const float* dtab_, float4* cand_, int stride_,
-                                         const float* sd, FoundList& FL) {
+    __device__ __forceinline__ void init(const DevGeom& G, const DevField& F, const ScanConst& P,
+                                         const DevLayer* s_lay, const uchar2* s_tab, const float* dtab_,
+                                         ListEntry* cand_, int stride_, const float* sd, FoundList& FL) {
         seed_state(sd, G.R0d, P.charge_dir, P.direction, s);
+        field_eval<KIND>(F, s.rx, s.ry, s.rz, bx, by, bz);
         dtab = dtab_;
         fired = (const uint32_t*)(dtab_ + G.n_wires);
         cand = cand_;
@@ -482,7 +493,7 @@ struct Tracer {
         const float rho = rho_of(x, y);
         if (in_chamber(s_tab, rho))
             visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(y, x), z,
-                         [&](int wire, float d, float cosa) {
+                         [&](int wire, float d, float cosa, int) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
                              if (dist_slope(x, y, z, tx, ty, tz, W, cosa, tp2) > 0.f)
@@ -499,26 +510,27 @@ struct Tracer {
         otx = s.tx;
         oty = s.ty;
         otz = s.tz;
-        rkn_step<KIND>(F, s, P.h, P.h6_lo);
+        rkn_step_fsal<KIND>(F, s, bx, by, bz, P.h, P.h6_lo);
         ++n;
     }
 
     // Minima of this lane's listed wires inside the last segment.
-    __device__ __forceinline__ void list_pass(const DevGeom& G, const ScanConst& P, FoundList& FL) {
+    __device__ __forceinline__ void list_pass(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
+                                              FoundList& FL) {
         if (over) return;
         const float kap = fabsf(s.lam) * P.b_max;
         for (int k = 0; k < nc; ++k) {
-            float4 e = cand[k * stride];
-            const int wire = __float_as_int(e.x);
+            const ListEntry e = cand[k * stride];
+            const int wire = (int)(e.key & 0xffffu);
             const float4 W = __ldg(G.wires + wire);
+            const float cosa = s_lay[e.key >> 16].cosa;
             float tp2;
-            const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, tp2);
-            if (e.y < 0.f && g1 >= 0.f)
+            const float g1 = dist_slope(s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, cosa, tp2);
+            if (e.g < 0.f && g1 >= 0.f)
                 found(P, FL, wire, part,
-                      seg_res(P, kap, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, e.w, e.z, e.y,
-                              g1));
-            e.y = g1;
-            cand[k * stride] = e;
+                      seg_res(P, kap, ox, oy, oz, otx, oty, otz, s.rx, s.ry, s.rz, s.tx, s.ty, s.tz, W, cosa,
+                              __ldg(dtab + wire), e.g, g1));
+            cand[k * stride].g = g1;
         }
     }
 
@@ -532,7 +544,7 @@ struct Tracer {
             const int pt = part;
             const float kap = fabsf(s.lam) * P.b_max;
             visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
-                         [&](int wire, float d, float cosa) {
+                         [&](int wire, float d, float cosa, int) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
                              const float g0 = dist_slope(ox, oy, oz, otx, oty, otz, W, cosa, tp2);
@@ -562,7 +574,7 @@ struct Tracer {
             // the whole window)
             const int pe = part;
             visit_window(s_lay, s_tab, dtab, fired, P.max_drift, P.band, P.d_win, rho, atan2f(ny, nx), nz,
-                         [&](int wire, float d, float cosa) {
+                         [&](int wire, float d, float cosa, int) {
                              const float4 W = __ldg(G.wires + wire);
                              float tp2;
                              if (dist_slope(nx, ny, nz, ntx, nty, ntz, W, cosa, tp2) < 0.f)
@@ -577,7 +589,7 @@ struct Tracer {
     __device__ __forceinline__ bool step(const DevGeom& G, const DevField& F, const ScanConst& P,
                                          const DevLayer* s_lay, const uchar2* s_tab, FoundList& FL) {
         advance(F, P);
-        list_pass(G, P, FL);
+        list_pass(G, P, s_lay, FL);
         return finish(G, P, s_lay, s_tab, FL);
     }
 

@@ -108,6 +108,7 @@ __device__ __forceinline__ int window_gather(const DevLayer* s_lay, const uchar2
 template <int KIND>
 struct WarpTracer {
     State s;
+    float bx, by, bz;                 // field at the last step's end estimate (at the seed before the first)
     float ox, oy, oz, otx, oty, otz;  // state before the last step (high words)
     const float* dtab;
     const uint32_t* fired;
@@ -220,9 +221,11 @@ struct WarpTracer {
     }
 
     // Seed state, the start-of-track minima and the first candidate list.
-    __device__ __forceinline__ void init(const DevGeom& G, const ScanConst& P, const DevLayer* s_lay,
-                                         const uchar2* s_tab, const float* dtab_, WarpFound* rec_, const float* sd) {
+    __device__ __forceinline__ void init(const DevGeom& G, const DevField& F, const ScanConst& P,
+                                         const DevLayer* s_lay, const uchar2* s_tab, const float* dtab_,
+                                         WarpFound* rec_, const float* sd) {
         seed_state(sd, G.R0d, P.charge_dir, P.direction, s);
+        field_eval<KIND>(F, s.rx, s.ry, s.rz, bx, by, bz);
         dtab = dtab_;
         fired = (const uint32_t*)(dtab_ + G.n_wires);
         rec = rec_;
@@ -269,7 +272,7 @@ struct WarpTracer {
         otx = s.tx;
         oty = s.ty;
         otz = s.tz;
-        rkn_step<KIND>(F, s, P.h, P.h6_lo);
+        rkn_step_fsal<KIND>(F, s, bx, by, bz, P.h, P.h6_lo);
         ++n;
     }
 

@@ -29,7 +29,7 @@ def _config():
 def _tracker(g, f, n0, warp_seeds=None):
     import paper_1908_01949_gb300 as cdc
     tr = cdc.Tracker(g, f, device=0, max_events=1, max_seeds=n0, max_hits=4096)
-    tr.ctx.cdc_set_scan_config(256, 16, warp_seeds)
+    tr.ctx.cdc_set_scan_config(128, 32, warp_seeds)
     return tr
 
 

@@ -163,10 +163,17 @@ def test_empty_call_and_a_seed_whose_event_has_no_hits():
         assert torch.equal(both[k][1:], alone[k]), k
 
 
-def test_three_turn_seed_with_more_than_128_classified_hits(field_map):
+@pytest.mark.parametrize("spread", [1.0, 0.1])
+def test_three_turn_seed_with_more_than_128_classified_hits(field_map, spread):
     """A three-turn signal classifies up to ~150 hits (the refine workload's
-    events); every one of them enters chi^2: n_used, chi^2 and the adjoint
-    gradient at seeds near the truth follow the oracle, with no overflow flag."""
+    events); every one of them enters chi^2: n_used and chi^2 follow the oracle,
+    with no overflow flag, and so does the adjoint gradient.  At seeds one
+    spread (3e-4 rad, 0.4 mm, 0.15, 0.15, 0.1 MeV/c) from the truth the gradient
+    is within 1e-4 relative.  Within a tenth of that spread the seeds sit near
+    the chi^2 minimum, where the gradient is a cancellation of per-hit terms 30
+    to 70 times its own size; there the FP32 error is bounded against the size
+    of those terms, 2 sqrt(chi^2 tr(S J^T J S)) in the scaled parameters S
+    (the Cauchy-Schwarz bound of sum_i 2 r_i |J_i|): within 2e-5 of it."""
     import torch
     import paper_1908_01949_gb300 as cdc
     g = S.make_geometry()
@@ -176,7 +183,7 @@ def test_three_turn_seed_with_more_than_128_classified_hits(field_map):
     sp = cdc.scan_params(h=2.0, max_steps=3500, lam=4.0, max_partitions=3)
     rp = cdc.refine_params(n_iter=0, sigma=0.2, checkpoint=128)
     rng = np.random.default_rng(5)
-    sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * 0.1
+    sig = np.array([3e-4, 0.4, 0.15, 0.15, 0.1]) * spread
     seeds = np.asarray([ev.truth_seeds[0] + rng.normal(0, 1, 5) * sig for _ in range(4)], np.float32)
     se = torch.zeros(len(seeds), dtype=torch.int32, device=tr.dev)
     out = tr.chi2_grad(se, torch.as_tensor(seeds, device=tr.dev), off, wid, dr, sp, rp)
@@ -189,12 +196,17 @@ def test_three_turn_seed_with_more_than_128_classified_hits(field_map):
         part, margin = _oracle_part(g, field_map, ev, sd, op)
         if (margin < 1e-3).any():
             continue
-        rc2, rg, _, rnu, _ = O.chi2(g, field_map, op, ev.wire_id, ev.drift.astype(np.float64), part, sd)
+        rc2, rg, jtj, rnu, _ = O.chi2(g, field_map, op, ev.wire_id, ev.drift.astype(np.float64), part, sd)
         assert rnu > 128, rnu                 # the case this test is about
         assert not (fl[i] & cdc.FLAG_FOUND_OVERFLOW)
         assert nu[i] == rnu
         assert abs(c2[i] - rc2) <= 1e-4 * rc2, (i, c2[i], rc2)
-        rel = np.linalg.norm((gr[i] - rg) * SCALE) / np.linalg.norm(rg * SCALE)
-        assert rel <= 1e-4, (i, rel, gr[i], rg)
+        err = np.linalg.norm((gr[i] - rg) * SCALE)
+        if spread >= 1.0:
+            rel = err / np.linalg.norm(rg * SCALE)
+            assert rel <= 1e-4, (i, rel, gr[i], rg)
+        else:
+            terms = 2.0 * np.sqrt(rc2 * np.trace(np.diag(SCALE) @ jtj @ np.diag(SCALE)))
+            assert err <= 2e-5 * terms, (i, err / terms, gr[i], rg)
         checked += 1
     assert checked >= 2
