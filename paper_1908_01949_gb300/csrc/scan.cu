@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(1024) order_blocks_kernel(int n_events, const 
 // its record of scored wires (record_slot).
 // BS threads per block: seven 128-thread blocks per SM (28 warps, 72 registers
 // per thread) or three 256-thread blocks (24 warps, 80 registers); the
-// shorter register budget costs a few spilled words outside the stepping loop
-// and its extra warps hide more of the field-load latency.
+// shorter register budget costs a few spilled words and its extra warps hide
+// more of the field-load latency.
 template <int KIND, int BS, int CHUNK>
 __global__ void __launch_bounds__(BS, 896 / BS) scan_kernel(DevGeom G, DevField F, ScanConst P, ScanIO io) {
     static_assert(CHUNK % LIST_M == 0, "candidate lists restart at chunk boundaries");

@@ -19,8 +19,8 @@
 // evaluates, for the listed wires only, the derivative of
 // the squared distance to the wire line, g = (r - m)_perp . t, at the new
 // state; a sign change from - to + brackets a local minimum of the distance,
-// which Newton iterations on the cubic Hermite interpolant of the segment
-// locate.  The window and band (host-computed) cover every wire whose distance
+// which a Newton step on the cubic Hermite interpolant of the segment
+// locates.  The window and band (host-computed) cover every wire whose distance
 // of closest approach can enter Eq. 1 below the cutoff, so the result equals
 // the brute-force definition.  Track ends count as minima when the distance is
 // still decreasing there.  If a list overflows, the tracer searches the window
@@ -262,12 +262,18 @@ __device__ __forceinline__ void visit_window(const DevLayer* s_lay, const uchar2
 }
 
 // Distance of closest approach inside a segment whose squared-distance
-// derivative changes sign from g0 < 0 to g1 >= 0: Newton iterations on the
+// derivative changes sign from g0 < 0 to g1 >= 0: a Newton step on the
 // cubic Hermite interpolant P(u) = r_j + H10 h t_j + H01 (r_j+1 - r_j) +
 // H11 h t_j+1 (u = tau h), started at the root of the linear interpolation of
-// the derivative.  (ax, ay, az) = r_j - m; (Dx, Dy, Dz) = r_j+1 - r_j.  Kept
-// out of line: it runs for a few percent of the steps and would otherwise set
-// the register budget of the whole stepping loop.
+// the derivative.  (ax, ay, az) = r_j - m; (Dx, Dy, Dz) = r_j+1 - r_j.  On
+// 2 mm segments of 250-400 mm radius passing stereo wires at 0-10 mm, the
+// start point alone leaves the distance up to 1.4e-4 mm off the interpolant's
+// minimum and one Newton step brings it to rounding level (FP64 model), so one
+// step is taken: a minimum runs on one lane of its warp, and each further
+// step cost 3-4 % of the coarse round.  Kept out of line: it runs for a few
+// percent of the steps and would otherwise set the register budget of the
+// whole stepping loop.
+constexpr int NEWTON_STEPS = 1;
 static __device__ __noinline__ float seg_doca(float ax, float ay, float az, float otx, float oty, float otz,
                                               float Dx, float Dy, float Dz, float ntx, float nty, float ntz,
                                               float4 W, float cosa, float g0, float g1, float h) {
@@ -275,7 +281,7 @@ static __device__ __noinline__ float seg_doca(float ax, float ay, float az, floa
     float u = h * (g0 / (g0 - g1));
     float wx, wy, wz, wd;
 #pragma unroll
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < NEWTON_STEPS; ++it) {
         const float t = u * ih, t2 = t * t;
         const float h10 = h * t * fmaf(t, t - 2.0f, 1.0f), h01 = t2 * fmaf(-2.0f, t, 3.0f), h11 = h * t2 * (t - 1.0f);
         wx = fmaf(h11, ntx, fmaf(h01, Dx, fmaf(h10, otx, ax)));
