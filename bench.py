@@ -557,7 +557,7 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
         tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
     seeds_coarse = int(np.prod(tmpl["n"][0]))
     seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
-    hp = cdc.hough_params(grid_template=tmpl)
+    hp = cdc.hough_params(grid_template=tmpl, **S.CFG2_HOUGH_RADII)
     sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
     ne = 1
@@ -684,6 +684,14 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
     h2d = int(np.mean([sum(q[a + "_h"].numel() * 4 for a in ("off", "wid", "dr")) for q in slots]))
     d2h = int(np.mean([q["out_E"].numel() * 4 + q["out_S"].numel() * 4 + q["out_P"].numel() + q["out_F"].numel() * 4
                        for q in slots]))
+    # does the Hough grid (top candidate) of each in-flight event hold the signal's first turn
+    held = 0
+    for k, q in enumerate(slots):
+        gr = cdc.tensor_to_grids(q["grid"])[0]
+        t = evs[k].truth_seeds[0]
+        half = 0.5 * np.asarray(gr["step"], np.float64) * np.asarray(gr["n"], np.float64)
+        dth = (float(gr["centre"][0]) - t[0] + np.pi) % (2 * np.pi) - np.pi
+        held += int(abs(dth) <= half[0] and abs(gr["centre"][2] - t[2]) <= half[2] and abs(gr["centre"][3] - t[3]) <= half[3])
     return {
         "workload": WORKLOAD_MULTI_TURN, "seeds_per_step": seeds_per_step, "ms_per_step": ms,
         "seeds_per_s": job_value(ws, seeds_per_step, ms), "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
@@ -698,6 +706,10 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
         "e2e": {"value": seeds_per_step / (e2e / 1e3), "unit": "seeds/s", "ms_per_step": e2e,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "launches_per_step": launches_per_step,
+        "hough": {"radii_mm": [hp.r_min_um / 1000.0, (hp.r_min_um + (hp.n_r - 1) * hp.r_step_um) / 1000.0],
+                  "grid_holds_signal": held, "events": n_in,
+                  "definition": "the (theta0, px0, py0) of the signal's first turn lies within the grid the top "
+                                "Hough candidate centres"},
         "l2": "256 MiB flush before every step, issued on the step's stream inside the timed events "
               "(~40 us per step counted against the result)",
         "_cpu": (evs[0], q0["grid"]),

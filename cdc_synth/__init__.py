@@ -510,6 +510,12 @@ def cfg1_case(index: int = 0):
     return g, f, ev, grid
 
 
+# Radii of the multi-turn configuration's circle Hough: a 104.97 MeV/c electron that makes two or three
+# turns before leaving |z| <= 750 mm has |pz| below ~30 MeV/c, so p_T >= ~97.4 MeV/c and a transverse
+# radius of at least 325 mm at 1 T; the window R_j = 325 + 5 j mm, j < 7, reaches 355 mm (p_T = 106 MeV/c).
+CFG2_HOUGH_RADII = {"n_r": 7, "r_min_um": 325000, "r_step_um": 5000}
+
+
 def cfg2_grid_template():
     """(z0, pz0) ranges of the multi-turn single-event workload: 40 x 25 points,
     35 mm and 4 MeV/c steps, centred at 0; (theta0, px0, py0) 10 x 10 x 10 at
