@@ -557,7 +557,7 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
         tmpl["n"][0][4] = 6                       # 10 x 40 x 10 x 10 x 6 = 240000 coarse seeds
     seeds_coarse = int(np.prod(tmpl["n"][0]))
     seeds_per_step = seeds_coarse + (N_ROUNDS - 1) * N_ZOOM * 243
-    hp = cdc.hough_params(grid_template=tmpl, **S.CFG2_HOUGH_RADII)
+    hp = cdc.hough_params(grid_template=tmpl, **S.CFG2_HOUGH)
     sp = cdc.scan_params(h=H, max_steps=MAX_STEPS, lam=LAM, max_partitions=MAX_PART, k=K, n_rounds=N_ROUNDS,
                          n_zoom=N_ZOOM, max_drift=MAX_DRIFT)
     ne = 1

@@ -510,10 +510,12 @@ def cfg1_case(index: int = 0):
     return g, f, ev, grid
 
 
-# Radii of the multi-turn configuration's circle Hough: a 104.97 MeV/c electron that makes two or three
-# turns before leaving |z| <= 750 mm has |pz| below ~30 MeV/c, so p_T >= ~97.4 MeV/c and a transverse
-# radius of at least 325 mm at 1 T; the window R_j = 325 + 5 j mm, j < 7, reaches 355 mm (p_T = 106 MeV/c).
-CFG2_HOUGH_RADII = {"n_r": 7, "r_min_um": 325000, "r_step_um": 5000}
+# Radii and angles of the multi-turn configuration's circle Hough: a 104.97 MeV/c electron that makes
+# two or three turns before leaving |z| <= 750 mm has |pz| below ~30 MeV/c, so p_T >= ~97.4 MeV/c and a
+# transverse radius of at least 325 mm at 1 T; the window R_j = 325 + 5 j mm, j < 7, reaches 355 mm
+# (p_T = 106 MeV/c).  1024 vote angles keep consecutive votes of a hit 2.2 mm apart at 355 mm, about a
+# 2 mm bin, where 512 would skip every other bin.
+CFG2_HOUGH = {"n_r": 7, "r_min_um": 325000, "r_step_um": 5000, "n_phi": 1024}
 
 
 def cfg2_grid_template():

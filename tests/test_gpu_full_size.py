@@ -20,7 +20,7 @@ N_SAMPLE = 1024
 def _config():
     import paper_1908_01949_gb300 as cdc
     tmpl = S.cfg2_grid_template()
-    hp = cdc.hough_params(grid_template=tmpl, **S.CFG2_HOUGH_RADII)
+    hp = cdc.hough_params(grid_template=tmpl, **S.CFG2_HOUGH)
     sp = cdc.scan_params(h=2.0, max_steps=3500, lam=4.0, max_partitions=3, k=8, n_rounds=10, n_zoom=4,
                          max_drift=8.0)
     return int(np.prod(tmpl["n"][0])), hp, sp
