@@ -69,16 +69,16 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # from one single-pass ncu capture of this benchmark's own launch; valid only for the kernel sources it was
 # taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
 TRAFFIC = {
-    "batched": {"bytes": 3954328832 + 8634023168, "shape": "128x32",
-                "csrc_sha256": "b1f67e9230f2655986e9e604d9370c0a233c8a0afefdfcfd3a1523463ce2f9cf"},
+    "batched": {"bytes": 3988608000 + 8637019392, "shape": "128x32",
+                "csrc_sha256": "65efe0eea7e6986df6aff81e536cc2641dd547122af17acf3650a1510368f36f"},
     "multi_turn": {"bytes": 67645184 + 82392832, "shape": "256x32",
                    "csrc_sha256": None},
 }
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 249.2, "fma_pipe_active_pct": 41.3,
-               "csrc_sha256": "b1f67e9230f2655986e9e604d9370c0a233c8a0afefdfcfd3a1523463ce2f9cf"}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 246.5, "fma_pipe_active_pct": 41.3,
+               "csrc_sha256": "65efe0eea7e6986df6aff81e536cc2641dd547122af17acf3650a1510368f36f"}
 FFMA_ITERS = 4096                # iterations of the FP32 throughput kernel (~4 ms on a GB300)
 
 
@@ -685,13 +685,19 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
     d2h = int(np.mean([q["out_E"].numel() * 4 + q["out_S"].numel() * 4 + q["out_P"].numel() + q["out_F"].numel() * 4
                        for q in slots]))
     # does the Hough grid (top candidate) of each in-flight event hold the signal's first turn
-    held = 0
+    held = held_any = 0
+    half = 0.5 * np.asarray(tmpl["step"][0], np.float64) * np.asarray(tmpl["n"][0], np.float64)
+
+    def holds(th, px, py, t):
+        dth = (float(th) - t[0] + np.pi) % (2 * np.pi) - np.pi
+        return abs(dth) <= half[0] and abs(px - t[2]) <= half[2] and abs(py - t[3]) <= half[3]
+
     for k, q in enumerate(slots):
-        gr = cdc.tensor_to_grids(q["grid"])[0]
         t = evs[k].truth_seeds[0]
-        half = 0.5 * np.asarray(gr["step"], np.float64) * np.asarray(gr["n"], np.float64)
-        dth = (float(gr["centre"][0]) - t[0] + np.pi) % (2 * np.pi) - np.pi
-        held += int(abs(dth) <= half[0] and abs(gr["centre"][2] - t[2]) <= half[2] and abs(gr["centre"][3] - t[3]) <= half[3])
+        gr = cdc.tensor_to_grids(q["grid"])[0]
+        held += int(gr["n"][0] > 0 and holds(gr["centre"][0], gr["centre"][2], gr["centre"][3], t))
+        cd = cdc.decode_candidates(q["cand"]).reshape(-1)[:int(q["ncand"][0].item())]
+        held_any += int(any(holds(c["theta0"], c["px0"], c["py0"], t) for c in cd))
     return {
         "workload": WORKLOAD_MULTI_TURN, "seeds_per_step": seeds_per_step, "ms_per_step": ms,
         "seeds_per_s": job_value(ws, seeds_per_step, ms), "rkn_steps_per_s": job_value(ws, rkn_per_step, ms),
@@ -707,9 +713,11 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "launches_per_step": launches_per_step,
         "hough": {"radii_mm": [hp.r_min_um / 1000.0, (hp.r_min_um + (hp.n_r - 1) * hp.r_step_um) / 1000.0],
-                  "grid_holds_signal": held, "events": n_in,
+                  "angles": hp.n_phi, "candidates": hp.max_cand,
+                  "grid_holds_signal": held, "some_candidate_grid_holds_signal": held_any, "events": n_in,
                   "definition": "the (theta0, px0, py0) of the signal's first turn lies within the grid the top "
-                                "Hough candidate centres"},
+                                "Hough candidate centres (or one of the grids cdc_candidate_grids centres on the "
+                                "candidates); the timed step scans the top candidate's grid"},
         "l2": "256 MiB flush before every step, issued on the step's stream inside the timed events "
               "(~40 us per step counted against the result)",
         "_cpu": (evs[0], q0["grid"]),

@@ -179,6 +179,23 @@ int cdc_hough_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const in
                     const cdc_hough_params* params, int32_t* acc, cdc_candidate* cand, int32_t* n_cand,
                     cdc_grid* grid_out, uint32_t* flags, void* stream);
 
+/* One seed grid per Hough candidate (sec. 2.1: each candidate circle gives a
+ * seed's theta0 and transverse momentum), so that the scan can search around
+ * every candidate instead of the top one only.  For event e and slot
+ * c < params->max_cand, grids[e * max_cand + c] = params->grid_template with
+ * (theta0, px0, py0) centred on candidate c, or the template with zero seeds
+ * where c >= n_cand[e] or the candidate's circle never crosses r = R0 (NaN
+ * centre); slot 0 equals the grid cdc_hough_seeds writes to grid_out.  To scan
+ * all of them, give cdc_scan_seeds each event's hits once per slot (the CSR
+ * with every event repeated max_cand times) and these grids.
+ * Device inputs: cand [n_events][max_cand], n_cand [n_events] as
+ * cdc_hough_seeds writes them.  Device output: grids [n_events * max_cand].
+ * Asynchronous on stream; allocates nothing.
+ * Errors: CDC_ERR_ARG (NULL, n_events < 0), CDC_ERR_RANGE (max_cand outside
+ * 1..64, n_events > 65535), CDC_ERR_CUDA. */
+int cdc_candidate_grids(cdc_ctx* ctx, int n_events, const cdc_hough_params* params, const cdc_candidate* cand,
+                        const int32_t* n_cand, cdc_grid* grids, void* stream);
+
 /* Seed scan (sec. 2.2, Eq. 1).  For every seed of grids[e] the track is
  * propagated by RKN steps of length h and scored
  *     E = sum over the event's hits of min( min_k (|DCA_k| - drift)^2, lambda ),

@@ -61,6 +61,15 @@ class Tracker:
                                  out["flags"], stream)
         return out
 
+    def candidate_grids(self, hough_out, params, stream=None):
+        """One seed grid per candidate slot of a hough() result: [n_events * max_cand]
+        grid records (slot-major within each event; zero seeds past the event's
+        candidates)."""
+        ne = int(hough_out["n_cand"].numel())
+        grids = self.torch.empty((ne * params.max_cand, GRID_BYTES), dtype=self.torch.uint8, device=self.dev)
+        self.ctx.cdc_candidate_grids(ne, params, hough_out["cand"], hough_out["n_cand"], grids, stream)
+        return grids
+
     def scan(self, hit_off, wire_id, drift, grids, params, want_E=False, want_topk0=True, want_hits=True,
              want_zoom_grids=False, n_seeds=None, stream=None):
         t = self.torch

@@ -36,7 +36,7 @@ EXPORTS = ["cdc_create", "cdc_destroy", "cdc_last_error", "cdc_load_geometry", "
            "cdc_hough_seeds", "cdc_scan_seeds", "cdc_refine_seeds", "cdc_chi2_grad", "cdc_propagate",
            "cdc_kernel_timer", "cdc_kernel_time", "cdc_set_scan_config", "cdc_get_scan_config", "cdc_tune_scan",
            "cdc_reserve_split", "cdc_scan_seeds_split", "cdc_extrapolate_turn", "cdc_classification_counts",
-           "cdc_common_hits", "cdc_fp32_peak", "cdc_efficiency_purity",
+           "cdc_common_hits", "cdc_fp32_peak", "cdc_efficiency_purity", "cdc_candidate_grids",
            "cdc_scan_seeds_noalloc"]
 
 
@@ -103,6 +103,7 @@ def lib():
                                      C.c_float, C.c_float]
         L.cdc_reserve.argtypes = [vp, C.c_int, i64, i64]
         L.cdc_hough_seeds.argtypes = [vp, C.c_int, vp, vp, P(cdc_hough_params), vp, vp, vp, vp, vp, vp]
+        L.cdc_candidate_grids.argtypes = [vp, C.c_int, P(cdc_hough_params), vp, vp, vp, vp]
         L.cdc_scan_seeds.argtypes = [vp, C.c_int, vp, vp, vp, vp, P(cdc_scan_params), vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp, vp]
         L.cdc_refine_seeds.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp, vp, vp, P(cdc_scan_params),
@@ -264,6 +265,13 @@ class Context:
             C.byref(params), _dev(acc, torch.int32, "acc", d), _dev(cand, torch.uint8, "cand", d),
             _dev(n_cand, torch.int32, "n_cand", d), _dev(grid_out, torch.uint8, "grid_out", d, True),
             _dev(flags, torch.int32, "flags", d), _stream(stream)))
+
+    def cdc_candidate_grids(self, n_events, params, cand, n_cand, grids, stream=None):
+        import torch
+        d = self.device
+        return self._check(self.L.cdc_candidate_grids(
+            self.h, int(n_events), C.byref(params), _dev(cand, torch.uint8, "cand", d),
+            _dev(n_cand, torch.int32, "n_cand", d), _dev(grids, torch.uint8, "grids", d), _stream(stream)))
 
     def cdc_scan_seeds(self, n_events, hit_off, wire_id, drift, grids, params, E, topk0, best_E, best_seed, hit_part,
                        hit_res2, zoom_grids, flags, steps, stream=None):

@@ -442,6 +442,20 @@ int cdc_hough_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int3
     return CDC_OK;
 }
 
+int cdc_candidate_grids(cdc_ctx* c, int n_events, const cdc_hough_params* p, const cdc_candidate* cand,
+                        const int32_t* n_cand, cdc_grid* grids, void* stream) {
+    if (!c) return CDC_ERR_ARG;
+    if (n_events < 0) return fail(c, CDC_ERR_ARG, "n_events < 0");
+    if (!p || !cand || !n_cand || !grids) return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (p->max_cand < 1 || p->max_cand > 64) return fail(c, CDC_ERR_RANGE, "max_cand outside 1..64");
+    if (n_events > 65535) return fail(c, CDC_ERR_RANGE, "more than 65535 events");
+    if (n_events == 0) return CDC_OK;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_candidate_grids(n_events, *p, cand, n_cand, grids, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "candidate grids launch");
+    return CDC_OK;
+}
+
 int cdc_scan_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int32_t* wire_id, const float* drift,
                    const cdc_grid* grids, const cdc_scan_params* p, float* E, uint64_t* topk0, float* best_E,
                    float* best_seed, int8_t* hit_part, float* hit_res2, cdc_grid* zoom_grids, uint32_t* flags,

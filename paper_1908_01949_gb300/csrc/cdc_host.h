@@ -120,6 +120,8 @@ struct HoughLaunch {
     uint32_t* flags;
 };
 cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const HoughLaunch& L, cudaStream_t st);
+cudaError_t launch_candidate_grids(int n_events, const cdc_hough_params& H, const cdc_candidate* cand,
+                                   const int32_t* n_cand, cdc_grid* grids, cudaStream_t st);
 
 // Refine (refine.cu).
 struct RefineLaunch {

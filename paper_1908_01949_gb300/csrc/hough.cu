@@ -315,4 +315,35 @@ cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const Houg
     return cudaGetLastError();
 }
 
+// One grid per (event, candidate slot): the template centred on the
+// candidate's seed, or a grid of zero seeds past the event's candidates and
+// where the circle never crosses r = R0 (the rule of the top candidate's
+// grid in hough_peaks_kernel).
+__global__ void candidate_grids_kernel(int n_events, int max_cand, cdc_grid tmpl, const cdc_candidate* __restrict__ cand,
+                                       const int32_t* __restrict__ n_cand, cdc_grid* grids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_events * max_cand) return;
+    const int e = i / max_cand, q = i - e * max_cand;
+    cdc_grid g = tmpl;
+    bool empty = q >= n_cand[e];
+    if (!empty) {
+        const cdc_candidate cd = cand[i];
+        g.centre[0] = cd.theta0;
+        g.centre[2] = cd.px0;
+        g.centre[3] = cd.py0;
+        empty = !(cd.theta0 == cd.theta0);
+    }
+    if (empty)
+        for (int a = 0; a < 5; ++a) g.n[a] = 0;
+    grids[i] = g;
+}
+
+cudaError_t launch_candidate_grids(int n_events, const cdc_hough_params& H, const cdc_candidate* cand,
+                                   const int32_t* n_cand, cdc_grid* grids, cudaStream_t st) {
+    const int n = n_events * H.max_cand;
+    candidate_grids_kernel<<<(n + 127) / 128, 128, 0, st>>>(n_events, H.max_cand, H.grid_template, cand, n_cand,
+                                                            grids);
+    return cudaGetLastError();
+}
+
 }  // namespace cdc

@@ -94,3 +94,47 @@ def test_zoom_rounds_follow_oracle_scores():
     assert abs(bE[0] - ref) <= E_REL * ref
     assert bE[0] <= coarse_best * (1 + E_REL)
     assert np.all(np.diff(bE) >= 0)
+
+
+def test_candidate_grids_centre_every_candidate(field_map):
+    """cdc_candidate_grids: slot 0 is the grid the Hough call writes; every
+    slot below the event's candidate count is the template centred on that
+    candidate's seed (theta0, px0, py0, the oracle's centres to float
+    rounding); the other slots hold zero seeds, and an event without hits
+    gets no seeds in any slot."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    events = [S.cfg2_case(i, field_map)[2] for i in range(3)]
+    empty = S.Event(wire_id=np.zeros(0, np.int32), drift=np.zeros(0, np.float32),
+                    truth_part=np.zeros(0, np.int8), truth_seeds=events[0].truth_seeds, n_turns=1)
+    events.insert(2, empty)
+    off, wid, dr = S.pack_events(events)
+    tr = tracker(g, field_map)
+    doff, dwid, _ = tr.events_to_device(off, wid, dr)
+    tmpl = S.cfg2_grid_template()
+    hp = cdc.hough_params(max_cand=6, grid_template=tmpl, **S.CFG2_HOUGH)
+    h = tr.hough(doff, dwid, hp)
+    cg = tr.candidate_grids(h, hp)
+    torch.cuda.synchronize()
+    grids = cdc.tensor_to_grids(cg).reshape(len(events), hp.max_cand)
+    top = cdc.tensor_to_grids(h["grid"])
+    ncand = h["n_cand"].cpu().numpy()
+    cand = cdc.decode_candidates(h["cand"]).reshape(len(events), hp.max_cand)
+    OH = O.hough_params(max_cand=6, **S.CFG2_HOUGH)
+    for e, ev in enumerate(events):
+        assert grids[e][0].tobytes() == top[e].tobytes(), e
+        _, rc, rcen = O.hough(g, OH, ev.wire_id)
+        assert ncand[e] == rc.shape[0]
+        for c in range(hp.max_cand):
+            gr = grids[e][c]
+            if c < ncand[e] and np.isfinite(cand[e][c]["theta0"]):
+                assert np.array_equal(gr["n"], tmpl["n"][0]) and np.array_equal(gr["step"], tmpl["step"][0])
+                assert gr["centre"][0] == cand[e][c]["theta0"] and gr["centre"][2] == cand[e][c]["px0"]
+                assert gr["centre"][3] == cand[e][c]["py0"]
+                assert gr["centre"][1] == tmpl["centre"][0][1] and gr["centre"][4] == tmpl["centre"][0][4]
+                assert np.allclose([gr["centre"][0], gr["centre"][2], gr["centre"][3]], rcen[c], rtol=1e-6, atol=1e-5)
+            else:
+                assert np.all(gr["n"] == 0), (e, c)
+    assert ncand[2] == 0 and np.all(grids[2]["n"] == 0)
+
