@@ -201,6 +201,46 @@ def test_propagated_positions_within_tolerance_per_metre(field_map, precision):
         assert worst < (1e-9 if precision == 1 else 1e-4), (precision, worst)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_propagation_beyond_a_small_field_map_follows_its_edge(precision):
+    """A map of only r <= 200 mm, |z| <= 200 mm: the tracks (r = 500 mm and
+    beyond) run outside it, where the field is the map's value at the nearest
+    edge point (the clamped interpolation of the oracle; the GPU's padded cell
+    table holds those edge values in its border ring).  Positions stay within
+    1e-4 mm per metre of the FP64 oracle (1e-9 for the FP64 stepper)."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    g2 = S.Geometry(R=g.R, alpha=g.alpha, N=g.N, phi_off=g.phi_off, z_half=5000.0, R0=g.R0, R_out=980.0)
+    f = S.solenoid_map(nr=101, nz=201, r_min=0.0, z_min=-200.0, dr=2.0, dz=2.0)
+    rng = np.random.default_rng(9)
+    seeds = []
+    for _ in range(32):
+        p, pz = 104.97, rng.uniform(-30, 30)
+        pt = math.sqrt(p * p - pz * pz)
+        th = rng.uniform(-math.pi, math.pi)
+        ang = th + rng.uniform(0.3, 1.2)
+        seeds.append([th, rng.uniform(-300, 300), pt * math.cos(ang), pt * math.sin(ang), pz])
+    seeds = np.asarray(seeds, np.float32)
+    tr = tracker(g2, f)
+    p = cdc.scan_params(h=2.0, max_steps=2000, lam=4.0, max_partitions=16)
+    out = tr.propagate(torch.as_tensor(seeds, device=tr.dev), p, every=250, n_rec=8, precision=precision)
+    torch.cuda.synchronize()
+    pos = out["pos"].cpu().numpy()
+    op = O.scan_params(h=2.0, max_steps=2000, lam=4.0, max_partitions=16)
+    worst, checked = 0.0, 0
+    for i in range(len(seeds)):
+        st, _, _ = O.propagate(g2, f, seeds[i].astype(np.float64), op)
+        for r in range(8):
+            j = 250 * (r + 1)
+            if j >= len(st) or not np.isfinite(pos[i, r, 0]):
+                continue
+            worst = max(worst, np.linalg.norm(pos[i, r] - st[j, :3]) / (j * 2.0 / 1000.0))
+            checked += 1
+    assert checked >= 64
+    assert worst < (1e-9 if precision == 1 else 1e-4), (precision, worst)
+
+
 def test_grid_with_more_blocks_than_the_order_table_keeps_natural_order():
     """A grid of 65 x 65 (z0, pz0) blocks (more than the 4096 the block order
     handles) is scanned in natural order; its scores and top-K still follow
