@@ -69,16 +69,16 @@ SCAN_SHAPES = [(256, 16), (256, 32), (128, 16), (128, 32)]   # order of cdc_tune
 # from one single-pass ncu capture of this benchmark's own launch; valid only for the kernel sources it was
 # taken on (csrc_digest: SHA-256 over the scan kernel's sources without comments), else null.
 TRAFFIC = {
-    "batched": {"bytes": 3988608000 + 8637019392, "shape": "128x32",
-                "csrc_sha256": "65efe0eea7e6986df6aff81e536cc2641dd547122af17acf3650a1510368f36f"},
+    "batched": {"bytes": 3974706176 + 8637271552, "shape": "128x32",
+                "csrc_sha256": "8e79243e112a36e8eb454c4e15b9aaba8195532ee9fcfbacd4fb956d002a745b"},
     "multi_turn": {"bytes": 67645184 + 82392832, "shape": "256x32",
                    "csrc_sha256": None},
 }
 # Executed FP32 operations per RKN step of the coarse-round kernel (FFMA = 2; ncu on the reduced
 # 240000-seed case, a per-step property of the code), same validity rule; the bench scales it by the
 # measured launch.
-FP32_COUNTS = {"fp32_ops_per_rkn_step": 246.5, "fma_pipe_active_pct": 41.3,
-               "csrc_sha256": "65efe0eea7e6986df6aff81e536cc2641dd547122af17acf3650a1510368f36f"}
+FP32_COUNTS = {"fp32_ops_per_rkn_step": 247.9, "fma_pipe_active_pct": 41.9,
+               "csrc_sha256": "8e79243e112a36e8eb454c4e15b9aaba8195532ee9fcfbacd4fb956d002a745b"}
 FFMA_ITERS = 4096                # iterations of the FP32 throughput kernel (~4 ms on a GB300)
 
 
@@ -627,9 +627,9 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
     for q in slots:
         q["ctx"].cdc_set_scan_config(*tuned, thr_ws)
     ctx.cdc_set_scan_config(*tuned, lat_ws)
-    # Hough vote + peaks; table clear + staging; block order of the coarse grid; per round prologue, scan,
-    # top-K partial + merge, best merge; a zoom grid build per zoom round; hit assignment
-    launches_per_step = 2 + 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
+    # Hough vote, maximum, slice peaks, merge; table clear + staging; block order of the coarse grid; per
+    # round prologue, scan, top-K partial + merge, best merge; a zoom grid build per zoom round; hit assignment
+    launches_per_step = 4 + 2 + 1 + 5 * N_ROUNDS + (N_ROUNDS - 1) + 1
     for i in range(args.warmup * n_in):
         step(slots[i % n_in])
     torch.cuda.synchronize()
@@ -684,6 +684,16 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
     h2d = int(np.mean([sum(q[a + "_h"].numel() * 4 for a in ("off", "wid", "dr")) for q in slots]))
     d2h = int(np.mean([q["out_E"].numel() * 4 + q["out_S"].numel() * 4 + q["out_P"].numel() + q["out_F"].numel() * 4
                        for q in slots]))
+    # the Hough call of one event alone (vote and peak search), CUDA events on its stream
+    hough_ms = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.cdc_hough_seeds(ne, q0["off"], q0["wid"], hp, q0["acc"], q0["cand"], q0["ncand"], q0["grid"],
+                            q0["hflags"], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hough_ms.append(e0.elapsed_time(e1))
     # does the Hough grid (top candidate) of each in-flight event hold the signal's first turn
     held = held_any = 0
     half = 0.5 * np.asarray(tmpl["step"][0], np.float64) * np.asarray(tmpl["n"][0], np.float64)
@@ -714,6 +724,7 @@ def multi_turn_leg(args, ws, rank, local, g, fm, flush, peak):
         "launches_per_step": launches_per_step,
         "hough": {"radii_mm": [hp.r_min_um / 1000.0, (hp.r_min_um + (hp.n_r - 1) * hp.r_step_um) / 1000.0],
                   "angles": hp.n_phi, "candidates": hp.max_cand,
+                  "ms_one_event": statistics.median(hough_ms),
                   "grid_holds_signal": held, "some_candidate_grid_holds_signal": held_any, "events": n_in,
                   "definition": "the (theta0, px0, py0) of the signal's first turn lies within the grid the top "
                                 "Hough candidate centres (or one of the grids cdc_candidate_grids centres on the "

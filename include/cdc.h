@@ -152,9 +152,9 @@ int cdc_load_field(cdc_ctx* ctx, int kind, float b0, const float* bz, const floa
 
 /* Size the context's workspace for calls with up to max_events events,
  * max_seeds seeds in total per scan round, and max_hits hits (besides the
- * per-seed scores and top-K segments, about 90 KB per event: the hit tables,
- * the coarse grid's block order and 64 records of scored wires kept for the
- * classification).  Compute calls never allocate; a call that exceeds the
+ * per-seed scores and top-K segments, about 190 KB per event: the hit tables,
+ * the coarse grid's block order, 64 records of scored wires kept for the
+ * classification and the Hough peak search's slice lists).  Compute calls never allocate; a call that exceeds the
  * reservation fails with CDC_ERR_NOT_LOADED.  Errors: CDC_ERR_ARG,
  * CDC_ERR_NOMEM. */
 int cdc_reserve(cdc_ctx* ctx, int max_events, int64_t max_seeds, int64_t max_hits);
@@ -174,7 +174,14 @@ int cdc_reserve(cdc_ctx* ctx, int max_events, int64_t max_seeds, int64_t max_hit
  * cand [n_events][max_cand], n_cand [n_events], grid_out [n_events] (nullable:
  * the top candidate's theta0, px0, py0 with the template's other fields; a
  * grid of zero seeds if there is no candidate), flags [n_events].
- * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED, CDC_ERR_CUDA. */
+ * The peak search uses the context's workspace (cdc_reserve with at least
+ * n_events events), so calls on one context must not overlap on the GPU.
+ * The first call with a new (n_r, r_min_um, r_step_um, n_phi) computes the
+ * integer vote offsets on the host and uploads them (a device allocation when
+ * the table grows, and a synchronous copy); later calls with those values
+ * allocate nothing and are asynchronous.
+ * Errors: CDC_ERR_ARG, CDC_ERR_RANGE, CDC_ERR_NOT_LOADED (geometry not loaded,
+ * or n_events above the reservation), CDC_ERR_CUDA. */
 int cdc_hough_seeds(cdc_ctx* ctx, int n_events, const int32_t* hit_off, const int32_t* wire_id,
                     const cdc_hough_params* params, int32_t* acc, cdc_candidate* cand, int32_t* n_cand,
                     cdc_grid* grid_out, uint32_t* flags, void* stream);

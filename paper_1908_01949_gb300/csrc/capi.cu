@@ -109,6 +109,8 @@ void free_workspace(Workspace& W) {
     dfree(W.recs);
     dfree(W.rec_count);
     dfree(W.run_best);
+    dfree(W.hough_max);
+    dfree(W.hough_keys);
     W = Workspace{};
 }
 
@@ -386,7 +388,9 @@ int cdc_reserve(cdc_ctx* c, int max_events, int64_t max_seeds, int64_t max_hits)
         (e = dalloc(W.perm, (size_t)max_events * PERM_CAP)) != cudaSuccess ||
         (e = dalloc(W.recs, (size_t)max_events * REC_SLOTS)) != cudaSuccess ||
         (e = dalloc(W.rec_count, (size_t)max_events)) != cudaSuccess ||
-        (e = dalloc(W.run_best, (size_t)max_events)) != cudaSuccess) {
+        (e = dalloc(W.run_best, (size_t)max_events)) != cudaSuccess ||
+        (e = dalloc(W.hough_max, (size_t)max_events)) != cudaSuccess ||
+        (e = dalloc(W.hough_keys, (size_t)max_events * HOUGH_SLICES * HOUGH_SLICE_KEYS)) != cudaSuccess) {
         free_workspace(W);
         return fail(c, CDC_ERR_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
     }
@@ -404,6 +408,8 @@ int cdc_hough_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int3
     if (n_events > 65535) return fail(c, CDC_ERR_RANGE, "more than 65535 events per Hough call");
     if (!p || !hit_off || !wire_id || !acc || !cand || !n_cand || !flags)
         return fail(c, CDC_ERR_ARG, "NULL argument");
+    if (n_events > c->W.max_events)
+        return fail(c, CDC_ERR_NOT_LOADED, "workspace too small: cdc_reserve at least n_events events");
     if (p->n_bins < 3 || p->n_bins > 4096 || p->bin_um < 2 || (p->bin_um & 1) || p->n_r < 1 || p->n_r > 256 ||
         p->n_phi < 1 || p->n_phi > 8192 || p->r_min_um < 0 || p->r_step_um < 0 || p->target_um < 0 ||
         p->min_peak < 1 || p->max_cand < 1 || p->max_cand > 64 || p->r_hist_half_um < 0)
@@ -436,7 +442,8 @@ int cdc_hough_seeds(cdc_ctx* c, int n_events, const int32_t* hit_off, const int3
     }
     cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_events, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "flags reset");
-    HoughLaunch L{n_events, hit_off, wire_id, c->d_offsets, acc, cand, n_cand, grid_out, flags};
+    HoughLaunch L{n_events, hit_off, wire_id, c->d_offsets, acc, cand, n_cand, grid_out, flags,
+                  c->W.hough_max, c->W.hough_keys};
     e = launch_hough(c->G, *p, L, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "Hough launch");
     return CDC_OK;

@@ -23,6 +23,7 @@ constexpr int FIRED_WORDS = CDC_MAX_WIRES / 32 + 3 * CDC_MAX_LAYERS;
 __host__ __device__ __forceinline__ size_t event_stride(int n_wires) { return (size_t)n_wires + FIRED_WORDS; }
 constexpr int SEG = 4096;                  // seeds per top-K segment
 constexpr uint64_t KEY_NONE = ~0ull;       // empty top-K slot
+constexpr unsigned FULL = 0xffffffffu;     // all lanes of a warp
 constexpr int ZOOM_GRID = 243;             // 3^5 seeds per zoom grid
 constexpr int ROUND_SHIFT = 27;            // best-list key: (round << 27) | index
 
@@ -406,6 +407,38 @@ __device__ __forceinline__ uint64_t make_key(float e, uint32_t idx) {
     uint32_t b = __float_as_uint(e);
     if (!(e >= 0.f)) b = 0x7f800000u;  // NaN or negative cannot occur; order them last
     return ((uint64_t)b << 32) | idx;
+}
+
+// Warp-resident ascending list of the K <= 64 smallest keys seen: lane l
+// holds entries l and 32 + l; every lane of the warp calls with its own key
+// (cand: whether it competes).
+__device__ __forceinline__ uint64_t list_at(uint64_t a, uint64_t b, int i) {
+    uint64_t va = __shfl_sync(FULL, a, i & 31);
+    uint64_t vb = __shfl_sync(FULL, b, i & 31);
+    return i < 32 ? va : vb;
+}
+
+__device__ __forceinline__ void list_insert(uint64_t& a, uint64_t& b, uint64_t key, bool cand, int K) {
+    const int lane = threadIdx.x & 31;
+    uint64_t thr = list_at(a, b, K - 1);
+    unsigned m = __ballot_sync(FULL, cand && key < thr);
+    while (m) {
+        int src = __ffs(m) - 1;
+        uint64_t k = __shfl_sync(FULL, key, src);
+        int p = __popc(__ballot_sync(FULL, a < k)) + __popc(__ballot_sync(FULL, b < k));
+        uint64_t pa = __shfl_up_sync(FULL, a, 1);
+        uint64_t pb = __shfl_up_sync(FULL, b, 1);
+        uint64_t a31 = __shfl_sync(FULL, a, 31);
+        if (lane == 0) pb = a31;
+        int ia = lane, ib = 32 + lane;
+        uint64_t na = ia < p ? a : (ia == p ? k : pa);
+        uint64_t nb = ib < p ? b : (ib == p ? k : pb);
+        a = na;
+        b = nb;
+        thr = list_at(a, b, K - 1);
+        m &= ~(1u << src);
+        m &= __ballot_sync(FULL, cand && key < thr);
+    }
 }
 
 }  // namespace cdc

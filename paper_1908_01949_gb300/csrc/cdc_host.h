@@ -8,6 +8,11 @@
 namespace cdc {
 
 // Device workspace owned by a context, sized by cdc_reserve.
+// Hough peak search: each event's accumulator is searched in HOUGH_SLICES
+// slices, each keeping its HOUGH_SLICE_KEYS (>= max_cand) best peaks.
+constexpr int HOUGH_SLICES = 64;
+constexpr int HOUGH_SLICE_KEYS = 64;
+
 struct Workspace {
     float* drift_tab = nullptr;            // [max_events][event_stride(n_wires)]: drifts, then fired-wire bits
     float* E = nullptr;                    // [e_cap] scores of the current round
@@ -22,6 +27,8 @@ struct Workspace {
     SeedRecord* recs = nullptr;            // [max_events][REC_SLOTS]: records of improving zoom-round seeds
     unsigned* rec_count = nullptr;         // [max_events]: records claimed in this call
     unsigned* run_best = nullptr;          // [max_events]: the event's best score so far (float bits)
+    int32_t* hough_max = nullptr;          // [max_events]: the Hough accumulator's maximum
+    uint64_t* hough_keys = nullptr;        // [max_events][HOUGH_SLICES][HOUGH_SLICE_KEYS]: peaks of each slice
     int max_events = 0;
     long long e_cap = 0, seg_cap = 0;
     int n_wires = 0;
@@ -118,6 +125,8 @@ struct HoughLaunch {
     int32_t* n_cand;
     cdc_grid* grid_out;
     uint32_t* flags;
+    int32_t* emax;             // [n_events] scratch: accumulator maxima
+    uint64_t* keys;            // [n_events][HOUGH_SLICES][HOUGH_SLICE_KEYS] scratch
 };
 cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const HoughLaunch& L, cudaStream_t st);
 cudaError_t launch_candidate_grids(int n_events, const cdc_hough_params& H, const cdc_candidate* cand,

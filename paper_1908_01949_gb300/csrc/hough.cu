@@ -10,8 +10,13 @@
 namespace cdc {
 
 constexpr int HOUGH_HITS = 64;      // hits staged per block iteration
-constexpr int PEAK_LIST = 2048;     // sorted list of selected peaks (only overflows for counts >= PEAK_HIST)
-constexpr int PEAK_HIST = 2048;     // histogram of peak counts
+constexpr int PEAK_BLOCKS = HOUGH_SLICES;    // blocks per event of the peak search, one slice of cells each
+constexpr int PEAK_KEYS = HOUGH_SLICE_KEYS;  // entries of a slice's list (max_cand <= 64)
+constexpr int PEAK_THREADS = 256;
+constexpr int SELECT_RUN = 16;      // counts each lane loads before testing them
+constexpr int HIST_CAP = 4096;      // radius-histogram bins of one pass over the hits (n_r <= 256)
+static_assert(PEAK_BLOCKS % (PEAK_THREADS / 32) == 0, "each warp merges the same number of slices");
+static_assert(PEAK_KEYS <= PEAK_THREADS, "a thread per candidate of a histogram pass");
 
 // Strict local maximum of the 3x3 neighbourhood; an equal neighbour with a
 // lower linear index wins.
@@ -87,155 +92,172 @@ __global__ void __launch_bounds__(256) hough_vote_kernel(const int32_t* __restri
     }
 }
 
-// One block per event: threshold, 3x3 peak test, ordering, radius histogram
-// and the seed centre on r = R0 (FP64).
-__global__ void __launch_bounds__(1024) hough_peaks_kernel(const int32_t* __restrict__ hit_off,
-                                                           const int32_t* __restrict__ wire_id,
-                                                           const int2* __restrict__ wire_um, int n_wires,
-                                                           cdc_hough_params H, double R0,
-                                                           const int32_t* __restrict__ acc, cdc_candidate* cand,
-                                                           int32_t* n_cand, cdc_grid* grid_out, uint32_t* flags) {
-    __shared__ unsigned long long s_list[PEAK_LIST];
-    __shared__ int s_hist2[PEAK_HIST];
-    __shared__ int s_wcnt[32];
-    __shared__ int s_n, s_max, s_t, s_found, s_chunk;
-    __shared__ int s_hist[256];
-    __shared__ int s_rbin[64];
-    const int e = blockIdx.x;
-    const int nb = H.n_bins;
+// The peak search runs in three launches so that an event's 262144 cells are
+// read by many blocks: the event's maximum (the threshold), each block's
+// PEAK_KEYS best peaks of its slice, and one block per event that merges the
+// slices' lists and forms the radius histogram and the seed centre.  A peak's
+// key is (~count << 32 | cell), so ascending keys are the order (count desc,
+// index asc) and the selection is exact however many peaks there are.
+__device__ __forceinline__ void peak_slice(long long ncell, int b, long long& c0, long long& c1) {
+    const long long per = (ncell + PEAK_BLOCKS - 1) / PEAK_BLOCKS;
+    c0 = min(ncell, (long long)b * per);
+    c1 = min(ncell, c0 + per);
+}
+
+__device__ __forceinline__ uint64_t peak_key(int v, long long c) {
+    return ((uint64_t)(0xffffffffu - (unsigned)v) << 32) | (uint32_t)c;
+}
+
+// The warps' lists of a block, merged into warp 0's (la, lb).
+__device__ __forceinline__ void merge_warp_lists(uint64_t& la, uint64_t& lb, int K,
+                                                 uint64_t (*s_keys)[PEAK_KEYS]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    s_keys[w][lane] = la;
+    s_keys[w][32 + lane] = lb;
+    __syncthreads();
+    if (w == 0)
+        for (int o = 1; o < PEAK_THREADS / 32; ++o) {
+            const uint64_t ka = s_keys[o][lane], kb = s_keys[o][32 + lane];
+            list_insert(la, lb, ka, ka != KEY_NONE, K);
+            list_insert(la, lb, kb, kb != KEY_NONE, K);
+        }
+}
+
+__global__ void __launch_bounds__(PEAK_THREADS) hough_max_kernel(int nb, const int32_t* __restrict__ acc,
+                                                                 int32_t* emax) {
+    __shared__ int s_max;
+    const int e = blockIdx.y;
     const long long ncell = (long long)nb * nb;
     const int32_t* A = acc + (size_t)e * ncell;
-    if (threadIdx.x == 0) {
-        s_n = 0;
-        s_max = 0;
-    }
+    long long c0, c1;
+    peak_slice(ncell, blockIdx.x, c0, c1);
+    if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     int mx = 0;
-    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) mx = max(mx, A[c]);
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) mx = max(mx, A[c]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(FULL, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(&s_max, mx);
     __syncthreads();
-    const int thr = max(H.min_peak, (s_max + 1) / 2);
-    // Exact selection of the max_cand best peaks without a bound on how many
-    // peaks the accumulator holds: a histogram of peak counts gives the count
-    // t of the last selected peak; peaks above t are collected directly (fewer
-    // than max_cand), peaks equal to t in increasing cell order until the list
-    // is full.
-    for (int b = threadIdx.x; b < PEAK_HIST; b += blockDim.x) s_hist2[b] = 0;
-    __syncthreads();
-    for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int v = A[c];
-        if (v >= thr && is_peak(A, nb, c, v)) atomicAdd(&s_hist2[min(v, PEAK_HIST - 1)], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int cum = 0, t = -1, lowest = -1;
-        for (int b = PEAK_HIST - 1; b >= 0; --b) {
-            if (s_hist2[b] == 0) continue;
-            lowest = b;
-            cum += s_hist2[b];
-            if (cum >= H.max_cand) {
-                t = b;
-                break;
-            }
+    if (threadIdx.x == 0 && s_max > 0) atomicMax(&emax[e], s_max);
+}
+
+// Peaks of one slice: count >= max(min_peak, ceil(max / 2)) and the strict
+// 3x3 maximum test; the block's max_cand smallest keys go to
+// keys[e][blockIdx.x][0 .. PEAK_KEYS).
+__global__ void __launch_bounds__(PEAK_THREADS) hough_select_kernel(cdc_hough_params H,
+                                                                    const int32_t* __restrict__ acc,
+                                                                    const int32_t* __restrict__ emax,
+                                                                    uint64_t* keys) {
+    __shared__ uint64_t s_keys[PEAK_THREADS / 32][PEAK_KEYS];
+    const int e = blockIdx.y, nb = H.n_bins, K = H.max_cand;
+    const long long ncell = (long long)nb * nb;
+    const int32_t* A = acc + (size_t)e * ncell;
+    const int thr = max(H.min_peak, (emax[e] + 1) / 2);
+    long long c0, c1;
+    peak_slice(ncell, blockIdx.x, c0, c1);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t la = KEY_NONE, lb = KEY_NONE;
+    // a warp takes runs of 32 x SELECT_RUN cells; the run's counts are loaded
+    // before any is tested, so the loads overlap instead of waiting in turn
+    for (long long base = c0 + (long long)w * 32 * SELECT_RUN; base < c1;
+         base += (long long)(PEAK_THREADS / 32) * 32 * SELECT_RUN) {  // warp-uniform
+        int v[SELECT_RUN];
+#pragma unroll
+        for (int k = 0; k < SELECT_RUN; ++k) {
+            const long long c = base + k * 32 + lane;
+            v[k] = c < c1 ? A[c] : 0;
         }
-        s_t = t >= 0 ? t : lowest;  // fewer peaks than max_cand: take them all
-    }
-    __syncthreads();
-    const int t_last = s_t;
-    if (t_last >= 0) {
-        const bool top = t_last == PEAK_HIST - 1;
-        for (long long c = threadIdx.x; c < ncell; c += blockDim.x) {
-            const int v = A[c];
-            if ((top ? v >= t_last : v > t_last) && is_peak(A, nb, c, v)) {
-                const int pos = atomicAdd(&s_n, 1);
-                if (pos < PEAK_LIST)
-                    s_list[pos] = ((unsigned long long)(0xffffffffu - (unsigned)v) << 32) | (unsigned)c;
-            }
-        }
-        __syncthreads();
-        if (!top) {
-            const int need = H.max_cand - s_n;  // ties at t_last, lowest cell index first
-            if (threadIdx.x == 0) s_found = 0;
-            __syncthreads();
-            for (long long base = 0; base < ncell && s_found < need; base += blockDim.x) {
-                const long long c = base + threadIdx.x;
-                const bool tie = c < ncell && A[c] == t_last && is_peak(A, nb, c, t_last);
-                const unsigned m = __ballot_sync(0xffffffffu, tie);
-                if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = __popc(m);
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int acc2 = 0;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                        const int k = s_wcnt[w];
-                        s_wcnt[w] = acc2;
-                        acc2 += k;
-                    }
-                    s_chunk = acc2;
-                }
-                __syncthreads();
-                if (tie) {
-                    const int pos = s_found + s_wcnt[threadIdx.x >> 5] + __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
-                    if (pos < need)
-                        s_list[s_n + pos] = ((unsigned long long)(0xffffffffu - (unsigned)t_last) << 32) | (unsigned)c;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) s_found += s_chunk;
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) s_n += min(s_found, need);
-            __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SELECT_RUN; ++k) {
+            const long long c = base + k * 32 + lane;
+            const bool peak = c < c1 && v[k] >= thr && is_peak(A, nb, c, v[k]);
+            if (__any_sync(FULL, peak)) list_insert(la, lb, peak ? peak_key(v[k], c) : KEY_NONE, peak, K);
         }
     }
-    const int np = min(s_n, PEAK_LIST);
-    if (threadIdx.x == 0 && s_n > PEAK_LIST) atomicOr(&flags[e], CDC_FLAG_FOUND_OVERFLOW);
-    for (int i = np + threadIdx.x; i < PEAK_LIST; i += blockDim.x) s_list[i] = ~0ull;
-    __syncthreads();
-    // bitonic sort of the selected peak keys: (count desc, index asc)
-    for (int k = 2; k <= PEAK_LIST; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < PEAK_LIST; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = s_list[i], b = s_list[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        s_list[i] = b;
-                        s_list[l] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    merge_warp_lists(la, lb, K, s_keys);
+    if (threadIdx.x < 32) {
+        uint64_t* out = keys + ((size_t)e * PEAK_BLOCKS + blockIdx.x) * PEAK_KEYS;
+        out[threadIdx.x] = la;
+        out[32 + threadIdx.x] = lb;
+    }
+}
+
+// One block per event: the slices' lists merged into the event's max_cand
+// best peaks, then per peak the radius histogram and the seed centre on
+// r = R0 (FP64).
+__global__ void __launch_bounds__(PEAK_THREADS) hough_finish_kernel(const int32_t* __restrict__ hit_off,
+                                                                    const int32_t* __restrict__ wire_id,
+                                                                    const int2* __restrict__ wire_um, int n_wires,
+                                                                    cdc_hough_params H, double R0,
+                                                                    const uint64_t* __restrict__ keys,
+                                                                    cdc_candidate* cand, int32_t* n_cand,
+                                                                    cdc_grid* grid_out, uint32_t* flags) {
+    __shared__ uint64_t s_keys[PEAK_THREADS / 32][PEAK_KEYS];
+    __shared__ uint64_t s_list[PEAK_KEYS];
+    __shared__ int s_hist[HIST_CAP];
+    __shared__ int s_rbin[PEAK_KEYS];
+    __shared__ int s_n;
+    const int e = blockIdx.x;
+    const int nb = H.n_bins, K = H.max_cand;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t la = KEY_NONE, lb = KEY_NONE;
+    {
+        constexpr int PER_WARP = PEAK_BLOCKS / (PEAK_THREADS / 32);  // slices merged by each warp
+        uint64_t ka[PER_WARP], kb[PER_WARP];
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {  // all loads first
+            const uint64_t* src = keys + ((size_t)e * PEAK_BLOCKS + w + i * (PEAK_THREADS / 32)) * PEAK_KEYS;
+            ka[i] = src[lane];
+            kb[i] = src[32 + lane];
         }
-    const int nc = min(np, H.max_cand);
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {
+            list_insert(la, lb, ka[i], ka[i] != KEY_NONE, K);
+            list_insert(la, lb, kb[i], kb[i] != KEY_NONE, K);
+        }
+    }
+    merge_warp_lists(la, lb, K, s_keys);
+    if (w == 0) {
+        s_list[lane] = la;
+        s_list[32 + lane] = lb;
+        const int n = __popc(__ballot_sync(FULL, la != KEY_NONE)) + __popc(__ballot_sync(FULL, lb != KEY_NONE));
+        if (lane == 0) s_n = min(n, K);
+    }
+    __syncthreads();
+    const int nc = s_n;
     const int h0 = hit_off[e], h1 = hit_off[e + 1];
-    for (int q = 0; q < nc; ++q) {
-        const int c = (int)(s_list[q] & 0xffffffffu);
-        const long long cx = (long long)H.origin_um + (long long)(c % nb) * H.bin_um + H.bin_um / 2;
-        const long long cy = (long long)H.origin_um + (long long)(c / nb) * H.bin_um + H.bin_um / 2;
-        for (int j = threadIdx.x; j < H.n_r; j += blockDim.x) s_hist[j] = 0;
+    // radius histograms of up to HIST_CAP / n_r candidates per pass over the hits
+    const int group = HIST_CAP / H.n_r;
+    for (int q0 = 0; q0 < nc; q0 += group) {
+        const int qn = min(group, nc - q0);
+        for (int i = threadIdx.x; i < qn * H.n_r; i += blockDim.x) s_hist[i] = 0;
         __syncthreads();
         for (int h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
-            const int w = wire_id[h];
-            if (w < 0 || w >= n_wires) continue;
-            const int2 X = wire_um[w];
-            const long long dx = X.x - cx, dy = X.y - cy;
-            const long long d2 = dx * dx + dy * dy;
-            for (int j = 0; j < H.n_r; ++j) {
-                const long long R = (long long)H.r_min_um + (long long)j * H.r_step_um;
-                const long long a = R - H.r_hist_half_um, b = R + H.r_hist_half_um;
-                if (d2 >= a * a && d2 < b * b) atomicAdd(&s_hist[j], 1);
+            const int wi = wire_id[h];
+            if (wi < 0 || wi >= n_wires) continue;
+            const int2 X = wire_um[wi];
+            for (int q = 0; q < qn; ++q) {
+                const int c = (int)(s_list[q0 + q] & 0xffffffffu);
+                const long long cx = (long long)H.origin_um + (long long)(c % nb) * H.bin_um + H.bin_um / 2;
+                const long long cy = (long long)H.origin_um + (long long)(c / nb) * H.bin_um + H.bin_um / 2;
+                const long long dx = X.x - cx, dy = X.y - cy;
+                const long long d2 = dx * dx + dy * dy;
+                for (int j = 0; j < H.n_r; ++j) {
+                    const long long R = (long long)H.r_min_um + (long long)j * H.r_step_um;
+                    const long long a = R - H.r_hist_half_um, b = R + H.r_hist_half_um;
+                    if (d2 >= a * a && d2 < b * b) atomicAdd(&s_hist[q * H.n_r + j], 1);
+                }
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < qn) {  // the most populated radius, ties to the lower j
             int bj = -1, bc = 0;
             for (int j = 0; j < H.n_r; ++j)
-                if (s_hist[j] > bc) {
-                    bc = s_hist[j];
+                if (s_hist[threadIdx.x * H.n_r + j] > bc) {
+                    bc = s_hist[threadIdx.x * H.n_r + j];
                     bj = j;
                 }
-            s_rbin[q] = bj;
+            s_rbin[q0 + threadIdx.x] = bj;
         }
         __syncthreads();
     }
@@ -310,8 +332,13 @@ cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const Houg
     const int n_pairs = H.n_r * H.n_phi;
     dim3 grid((n_pairs + 255) / 256, 8, L.n_events);
     hough_vote_kernel<<<grid, 256, 0, st>>>(L.hit_off, L.wire_id, G.wire_um, G.n_wires, L.offsets, H, L.acc);
-    hough_peaks_kernel<<<L.n_events, 1024, 0, st>>>(L.hit_off, L.wire_id, G.wire_um, G.n_wires, H, G.R0d, L.acc,
-                                                    L.cand, L.n_cand, L.grid_out, L.flags);
+    err = cudaMemsetAsync(L.emax, 0, sizeof(int32_t) * L.n_events, st);
+    if (err != cudaSuccess) return err;
+    const dim3 pg(PEAK_BLOCKS, L.n_events);
+    hough_max_kernel<<<pg, PEAK_THREADS, 0, st>>>(H.n_bins, L.acc, L.emax);
+    hough_select_kernel<<<pg, PEAK_THREADS, 0, st>>>(H, L.acc, L.emax, L.keys);
+    hough_finish_kernel<<<L.n_events, PEAK_THREADS, 0, st>>>(L.hit_off, L.wire_id, G.wire_um, G.n_wires, H, G.R0d,
+                                                             L.keys, L.cand, L.n_cand, L.grid_out, L.flags);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,6 @@
 
 namespace cdc {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr float NOT_FIRED = 3.0e38f;   // drift-table sentinel (above any valid drift)
 
 // ---------------------------------------------------------------- staging
@@ -309,36 +308,6 @@ __global__ void __launch_bounds__(BS, 896 / BS) scan_kernel(DevGeom G, DevField 
 }
 
 // ------------------------------------------------------------------ top-K
-// Warp-resident sorted list of up to 64 keys: lane l holds entries l and 32+l.
-__device__ __forceinline__ uint64_t list_at(uint64_t a, uint64_t b, int i) {
-    uint64_t va = __shfl_sync(FULL, a, i & 31);
-    uint64_t vb = __shfl_sync(FULL, b, i & 31);
-    return i < 32 ? va : vb;
-}
-
-__device__ __forceinline__ void list_insert(uint64_t& a, uint64_t& b, uint64_t key, bool cand, int K) {
-    const int lane = threadIdx.x & 31;
-    uint64_t thr = list_at(a, b, K - 1);
-    unsigned m = __ballot_sync(FULL, cand && key < thr);
-    while (m) {
-        int src = __ffs(m) - 1;
-        uint64_t k = __shfl_sync(FULL, key, src);
-        int p = __popc(__ballot_sync(FULL, a < k)) + __popc(__ballot_sync(FULL, b < k));
-        uint64_t pa = __shfl_up_sync(FULL, a, 1);
-        uint64_t pb = __shfl_up_sync(FULL, b, 1);
-        uint64_t a31 = __shfl_sync(FULL, a, 31);
-        if (lane == 0) pb = a31;
-        int ia = lane, ib = 32 + lane;
-        uint64_t na = ia < p ? a : (ia == p ? k : pa);
-        uint64_t nb = ib < p ? b : (ib == p ? k : pb);
-        a = na;
-        b = nb;
-        thr = list_at(a, b, K - 1);
-        m &= ~(1u << src);
-        m &= __ballot_sync(FULL, cand && key < thr);
-    }
-}
-
 // One warp per segment of SEG seeds: the K lowest (E, index) keys.
 __global__ void topk_partial_kernel(const float* __restrict__ E, const long long* __restrict__ seed_off,
                                     const int* __restrict__ seg_off, int n_events,

@@ -138,3 +138,49 @@ def test_candidate_grids_centre_every_candidate(field_map):
                 assert np.all(gr["n"] == 0), (e, c)
     assert ncand[2] == 0 and np.all(grids[2]["n"] == 0)
 
+
+
+def test_hough_peak_selection_with_many_tied_peaks(field_map):
+    """The peak search runs over slices of the accumulator in separate blocks;
+    its max_cand best peaks (count desc, cell index asc) equal the oracle's
+    when the accumulator holds far more equal-count peaks than max_cand: events
+    of one, two and five hits (counts of a few votes, thousands of tied local
+    maxima spread over every slice) and a full event, at max_cand = 64 and 1.
+    A call with more events than the reservation is refused."""
+    import torch
+    import paper_1908_01949_gb300 as cdc
+    g = S.make_geometry()
+    full = S.cfg2_case(0, field_map)[2]
+    rng = np.random.default_rng(11)
+
+    def sparse(n):
+        w = rng.choice(g.n_wires, size=n, replace=False).astype(np.int32)
+        return S.Event(wire_id=w, drift=np.zeros(n, np.float32), truth_part=np.zeros(n, np.int8),
+                       truth_seeds=full.truth_seeds, n_turns=1)
+
+    events = [sparse(1), sparse(2), full, sparse(5)]
+    off, wid, dr = S.pack_events(events)
+    tr = tracker(g, field_map)
+    doff, dwid, _ = tr.events_to_device(off, wid, dr)
+    for mc in (64, 1):
+        hp = cdc.hough_params(max_cand=mc, min_peak=1, grid_template=S.cfg2_grid_template(), **S.CFG2_HOUGH)
+        out = tr.hough(doff, dwid, hp)
+        torch.cuda.synchronize()
+        cand = cdc.decode_candidates(out["cand"]).reshape(len(events), mc)
+        ncand = out["n_cand"].cpu().numpy()
+        OH = O.hough_params(max_cand=mc, min_peak=1, **S.CFG2_HOUGH)
+        for e, ev in enumerate(events):
+            racc, rc, rcen = O.hough(g, OH, ev.wire_id)
+            assert ncand[e] == rc.shape[0], (mc, e)
+            got = np.stack([cand[e]["ix"], cand[e]["iy"], cand[e]["count"], cand[e]["r_bin"]], 1)[:ncand[e]]
+            assert np.array_equal(got, rc), (mc, e)
+            cen = np.stack([cand[e]["theta0"], cand[e]["px0"], cand[e]["py0"]], 1)[:ncand[e]]
+            assert np.allclose(cen, rcen, rtol=1e-6, atol=1e-5, equal_nan=True)
+            if mc == 64:
+                # the case is really exercised: the oracle's longer list ties across the 64th slot
+                _, big, _ = O.hough(g, O.hough_params(max_cand=1024, min_peak=1, **S.CFG2_HOUGH), ev.wire_id)
+                assert big.shape[0] > 64 and big[63, 2] == big[64, 2], e
+    small = tracker(g, field_map, max_events=2, max_seeds=1024, max_hits=4096)
+    soff, swid, _ = small.events_to_device(off, wid, dr)
+    with pytest.raises(cdc.CdcError, match="reserve"):
+        small.hough(soff, swid, cdc.hough_params(grid_template=S.cfg2_grid_template()))
