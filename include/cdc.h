@@ -13,7 +13,9 @@
  *     tensors).  The caller owns every buffer it passes.
  *   - Compute calls are asynchronous on the given stream (cudaStream_t passed
  *     as void*, NULL = legacy default stream); they allocate nothing and do not
- *     synchronise.  They return CDC_OK once the work is enqueued.
+ *     synchronise (one exception: cdc_hough_seeds uploads its vote-offset table
+ *     when its radii or angles change).  They return CDC_OK once the work is
+ *     enqueued.
  *   - Errors: every call returns a cdc_status; cdc_last_error(ctx) gives a
  *     one-line reason.  Argument errors are detected before anything is
  *     enqueued.  Per-event conditions (step cap reached, full found-hit list,
