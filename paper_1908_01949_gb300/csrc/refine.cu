@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "cdc_dev.cuh"
 #include "cdc_host.h"
 #include "tracer.cuh"
@@ -946,6 +948,25 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
     a.flags[i] = flags;
 }
 
+// Shared-memory share of the SM for the refine kernel: just what its resident
+// blocks (4, the launch bounds) need, so that the rest of the SM's on-chip
+// memory serves as L1 for the threads' local stacks (classified hits,
+// checkpoints, the adjoint's buffer).  Set as a preference before each launch.
+template <class K>
+static cudaError_t prefer_l1(K kernel) {
+    constexpr int RESIDENT = 4;
+    cudaFuncAttributes fa;
+    cudaError_t err = cudaFuncGetAttributes(&fa, kernel);
+    int dev = 0, per_sm = 0, reserved = 0;
+    if (err == cudaSuccess) err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (err != cudaSuccess || per_sm <= 0) return err;
+    const long long need = (long long)RESIDENT * ((long long)fa.sharedSizeBytes + reserved);
+    const int pct = (int)std::min<long long>(100, (need * 100 + per_sm - 1) / per_sm);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& P, const RefineLaunch& L,
                           float* drift_tab, int num_sms, int do_gn, cudaStream_t st) {
     cudaError_t err = launch_stage(G, L.n_events, L.hit_off, L.wire_id, L.drift, P.max_drift, drift_tab, nullptr,
@@ -955,10 +976,13 @@ cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& 
               {L.scale[0], L.scale[1], L.scale[2], L.scale[3], L.scale[4]}, L.checkpoint, L.seeds_out, L.chi2, L.grad,
               L.n_used, L.flags};
     const int bs = 128, nb = (L.n_seeds + bs - 1) / bs;
-    if (F.kind == 0)
+    if (F.kind == 0) {
+        if ((err = prefer_l1(refine_kernel<0>)) != cudaSuccess) return err;
         refine_kernel<0><<<nb, bs, 0, st>>>(G, F, P, a, do_gn);
-    else
+    } else {
+        if ((err = prefer_l1(refine_kernel<1>)) != cudaSuccess) return err;
         refine_kernel<1><<<nb, bs, 0, st>>>(G, F, P, a, do_gn);
+    }
     return cudaGetLastError();
 }
 
