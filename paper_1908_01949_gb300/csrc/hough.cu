@@ -345,7 +345,7 @@ cudaError_t launch_hough(const DevGeom& G, const cdc_hough_params& H, const Houg
 // One grid per (event, candidate slot): the template centred on the
 // candidate's seed, or a grid of zero seeds past the event's candidates and
 // where the circle never crosses r = R0 (the rule of the top candidate's
-// grid in hough_peaks_kernel).
+// grid in hough_finish_kernel).
 __global__ void candidate_grids_kernel(int n_events, int max_cand, cdc_grid tmpl, const cdc_candidate* __restrict__ cand,
                                        const int32_t* __restrict__ n_cand, cdc_grid* grids) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
