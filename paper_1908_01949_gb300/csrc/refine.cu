@@ -820,15 +820,21 @@ __device__ double chi2_adjoint(const DevGeom& G, const DevField& F, const ScanCo
     return chi2;
 }
 
-// Thread per seed.  Capped at 128 registers (four 128-thread blocks per SM,
-// a few hundred bytes of spills): the ~225 the code would take leave two
-// blocks per SM, half the latency hiding and, for 65536 seeds, 1.7 waves
-// (measured 128 -> 118 ms for 65536 seeds x 5 iterations).
+// Thread per seed.  Capped at 128 registers (512 threads per SM, a few
+// hundred bytes of spills): the ~225 the code would take leave half the
+// threads, half the latency hiding and, for 65536 seeds, 1.7 waves (measured
+// 128 -> 118 ms for 65536 seeds x 5 iterations).  64-thread blocks: 65536
+// seeds spread as 6-7 blocks over each SM instead of 3-4 blocks of 128
+// (91.0 against 93.0 ms; 32-thread blocks, whose shared tables leave less L1,
+// 99.5 ms).
+constexpr int REFINE_BLOCK = 64;
+
 template <int KIND>
-__global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, ScanConst P, RefArgs a, int do_gn) {
+__global__ void __launch_bounds__(REFINE_BLOCK, 512 / REFINE_BLOCK)
+    refine_kernel(DevGeom G, DevField F, ScanConst P, RefArgs a, int do_gn) {
     __shared__ DevLayer s_lay[CDC_MAX_LAYERS];
     __shared__ uchar2 s_tab[TAB_N];
-    __shared__ ListEntry s_cand[LIST_CAP][128];
+    __shared__ ListEntry s_cand[LIST_CAP][REFINE_BLOCK];
     for (int i = threadIdx.x; i < G.n_layers; i += blockDim.x) s_lay[i] = G.layers[i];
     for (int i = threadIdx.x; i < TAB_N; i += blockDim.x) s_tab[i] = G.tab[i];
     __syncthreads();
@@ -859,7 +865,7 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
     {
         Tracer<KIND> T;
         FoundList FL;
-        T.init(G, F, P, s_lay, s_tab, dtab, &s_cand[0][threadIdx.x], 128, sf, FL);
+        T.init(G, F, P, s_lay, s_tab, dtab, &s_cand[0][threadIdx.x], REFINE_BLOCK, sf, FL);
         while (T.step(G, F, P, s_lay, s_tab, FL))
             if (T.n % LIST_M == 0) {
                 T.rebuild(G, P, s_lay, s_tab);
@@ -949,12 +955,12 @@ __global__ void __launch_bounds__(128, 4) refine_kernel(DevGeom G, DevField F, S
 }
 
 // Shared-memory share of the SM for the refine kernel: just what its resident
-// blocks (4, the launch bounds) need, so that the rest of the SM's on-chip
+// blocks (the launch bounds) need, so that the rest of the SM's on-chip
 // memory serves as L1 for the threads' local stacks (classified hits,
 // checkpoints, the adjoint's buffer).  Set as a preference before each launch.
 template <class K>
 static cudaError_t prefer_l1(K kernel) {
-    constexpr int RESIDENT = 4;
+    constexpr int RESIDENT = 512 / REFINE_BLOCK;
     cudaFuncAttributes fa;
     cudaError_t err = cudaFuncGetAttributes(&fa, kernel);
     int dev = 0, per_sm = 0, reserved = 0;
@@ -975,7 +981,7 @@ cudaError_t launch_refine(const DevGeom& G, const DevField& F, const ScanConst& 
     RefArgs a{L.n_seeds, L.seed_event, L.seeds, L.n_events, L.hit_off, drift_tab, L.n_iter, L.sigma,
               {L.scale[0], L.scale[1], L.scale[2], L.scale[3], L.scale[4]}, L.checkpoint, L.seeds_out, L.chi2, L.grad,
               L.n_used, L.flags};
-    const int bs = 128, nb = (L.n_seeds + bs - 1) / bs;
+    const int bs = REFINE_BLOCK, nb = (L.n_seeds + bs - 1) / bs;
     if (F.kind == 0) {
         if ((err = prefer_l1(refine_kernel<0>)) != cudaSuccess) return err;
         refine_kernel<0><<<nb, bs, 0, st>>>(G, F, P, a, do_gn);
