@@ -49,6 +49,9 @@ class Tracker:
                 t.as_tensor(np.asarray(drift, np.float32), device=self.dev))
 
     def hough(self, hit_off, wire_id, params, stream=None):
+        """Circle Hough of every event (cdc_hough_seeds): accumulators, candidates,
+        the top candidate's seed grid and flags.  The peak search uses this
+        tracker's workspace, so the events may number at most its max_events."""
         t = self.torch
         ne = int(hit_off.numel()) - 1
         nb = params.n_bins
